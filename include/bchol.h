@@ -1,0 +1,145 @@
+/*
+ * bchol.h -- C ABI of the GB300 banded Cholesky library (libbchol.so).
+ *
+ * Method: F. Liu, A. Fredriksson, S. Markidis, "Parallel Cholesky
+ * Factorization for Banded Matrices using OpenMP Tasks" (arXiv 2305.04635).
+ * The library factors a symmetric positive-definite band matrix A = L L^T
+ * (Sec. 2.1, Sec. 3, Algorithm 1) and solves A X = B with the factor.
+ *
+ * Storage (Sec. 3: the standard LAPACK band format, kept to avoid any format
+ * conversion): A of order n with half-bandwidth k ("number of super- and
+ * sub-diagonals", Sec. 1 and Sec. 3.1) is held by its lower band in a
+ * column-major array `ab` with leading dimension ldab >= k+1:
+ *     A(i,j) = ab[(i-j) + j*ldab]      for 0 <= j <= i <= min(n-1, j+k).
+ * Rows d >= k+1 of the array (when ldab > k+1) and the slots (d, j) with
+ * j + d >= n hold no matrix entry; the library never reads or writes them.
+ * k >= n is accepted and treated as k = n-1 (a dense lower triangle).
+ *
+ * Conventions shared by every entry point:
+ *  - All matrix and vector pointers are DEVICE pointers owned by the caller.
+ *    The library never frees or keeps them past the call.
+ *  - Every call is asynchronous on the handle's CUDA stream.  Argument errors
+ *    are found on the host before any launch and return BCHOL_ERR_ARG with
+ *    nothing launched.  A CUDA launch or copy failure returns BCHOL_ERR_CUDA.
+ *  - Numerical failure (a pivot that is not > 0, NaN included) is reported the
+ *    LAPACK way through a device-resident `info`; the call itself still
+ *    returns BCHOL_OK.  bchol_get_info synchronises and reads it.
+ *  - Every wait inside a kernel is bounded in time.  A wait that runs out
+ *    stops the kernel cleanly and records BCHOL_ERR_TIMEOUT in the handle;
+ *    bchol_get_info reports it.
+ *  - The handle owns internal device workspace (ready flags, a task counter,
+ *    inverted diagonal blocks).  It is taken from a buffer the caller lends
+ *    with bchol_set_workspace, else allocated with cudaMalloc on first use and
+ *    kept until bchol_destroy.  Calls on one handle must not overlap.
+ */
+#ifndef BCHOL_H
+#define BCHOL_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bchol_handle_s* bchol_handle_t;
+
+typedef enum {
+  BCHOL_OK = 0,
+  BCHOL_ERR_ARG = -1,      /* invalid argument; nothing was launched */
+  BCHOL_ERR_NOT_SPD = 1,   /* some info > 0: a leading minor is not positive definite */
+  BCHOL_ERR_TIMEOUT = 2,   /* a bounded in-kernel wait ran out; results are unspecified */
+  BCHOL_ERR_CUDA = 3,      /* a CUDA runtime call failed */
+  BCHOL_ERR_ALLOC = 4,     /* workspace allocation failed, or the lent workspace is too small */
+  BCHOL_ERR_UNSUPPORTED = 5
+} bchol_status_t;
+
+/* Create a handle bound to `stream` (a cudaStream_t; NULL = the legacy default
+ * stream) on the current device.  No device memory is allocated here. */
+bchol_status_t bchol_create(bchol_handle_t* handle, void* stream);
+
+/* Release the handle and any workspace it allocated itself. */
+bchol_status_t bchol_destroy(bchol_handle_t handle);
+
+/* Rebind the handle to another stream. */
+bchol_status_t bchol_set_stream(bchol_handle_t handle, void* stream);
+
+/* Lend the handle a device buffer (16-byte aligned) for its workspace, or
+ * pass NULL/0 to go back to self-allocated workspace.  The buffer must stay
+ * valid while calls that use it may be running. */
+bchol_status_t bchol_set_workspace(bchol_handle_t handle, void* dev_ptr, size_t bytes);
+
+/* Bytes of workspace that bchol_factor / bchol_solve need for order n and
+ * half-bandwidth k with the handle's current settings. */
+size_t bchol_workspace_size(bchol_handle_t handle, int n, int k);
+
+/*
+ * bchol_factor -- A = L L^T in place (Algorithm 1 and its cross-iteration
+ * overlap, Sec. 3; the factor is the unique one of Sec. 2.1).
+ *   n, k      order and half-bandwidth, n >= 0, k >= 0
+ *   ab        device, the lower band of A as above; overwritten by L
+ *   ldab      leading dimension, ldab >= k+1
+ *   info_dev  device int, written by the kernel: 0 on success, or j > 0 when
+ *             the leading minor of order j is not positive definite (LAPACK
+ *             pbtrf convention).  When j > 0 the contents of ab are unspecified.
+ * The whole factorization is one persistent kernel launch (plus one memset
+ * of the ready flags).  Tiles are b x b with b chosen from k (32 or 64).
+ */
+bchol_status_t bchol_factor(bchol_handle_t handle, int n, int k, double* ab, int ldab, int* info_dev);
+
+/*
+ * bchol_solve -- X = A^{-1} B from the factor that bchol_factor left in ab
+ * (LAPACK pbtrs semantics, lower): L Y = B by forward substitution, then
+ * L^T X = Y by back substitution.  The paper solves no systems itself; its
+ * motivation is the repeated banded solves of an interior-point method
+ * (Sec. 1 and Sec. 2).
+ *   ab, ldab  device, the factor L in band storage (read only)
+ *   b, ldb    device, B is n x nrhs column-major with ldb >= max(1,n);
+ *             overwritten by X
+ */
+bchol_status_t bchol_solve(bchol_handle_t handle, int n, int k, int nrhs, const double* ab, int ldab,
+                           double* b, int ldb);
+
+/* Wait for the handle's stream, copy `count` device info words to
+ * info_host, and return BCHOL_ERR_TIMEOUT if a bounded wait ran out since the
+ * last call, else BCHOL_ERR_NOT_SPD if any info > 0, else BCHOL_OK.  Clears
+ * the timeout record. */
+bchol_status_t bchol_get_info(bchol_handle_t handle, const int* info_dev, int count, int* info_host);
+
+/* Settings.  tile: 0 = automatic, else 16, 32 or 64.  wait_limit_ms: the time
+ * budget of one in-kernel wait (default 2000 ms).  ctas_per_sm: persistent
+ * CTAs per SM for the factor kernel (0 = automatic). */
+bchol_status_t bchol_set_tile(bchol_handle_t handle, int tile);
+bchol_status_t bchol_set_wait_limit_ms(bchol_handle_t handle, int wait_limit_ms);
+bchol_status_t bchol_set_ctas_per_sm(bchol_handle_t handle, int ctas_per_sm);
+
+/* Test hook for the failure path.  While set to a tile (I, J) >= 0, the
+ * factor kernel's waits on the ready flag of tile (I, J) (b x b tiles, block
+ * row I, block column J, 0 <= I-J <= ceil(k/b)) get a target that is never
+ * reached, so the first such wait runs out after the wait limit: the kernel
+ * stops cleanly and bchol_get_info reports BCHOL_ERR_TIMEOUT.  (-1, -1)
+ * turns it off (the default). */
+bchol_status_t bchol_set_stall_tile(bchol_handle_t handle, int I, int J);
+
+/* Schedule query (host only, no GPU needed).  The factor kernel walks the
+ * tasks of the tiled factorization in ticket order: step s (one outer
+ * iteration of Algorithm 1, Sec. 3) is POTRF(s) (type 0), then for each panel
+ * row I = s+1..s+m the TRSM(I, s) (type 1) followed by the updates
+ * UPD(I, J, s) for J = s+1..I (type 2: A_IJ -= L_Is L_Js^T), with
+ * m = min(ceil(k/tile), ceil(n/tile)-1-s).  bchol_plan_task_count returns the
+ * number of tasks (or -1 on bad arguments); bchol_plan_task decodes one
+ * ticket into (type, s, I, J) in tile units.  tile is 16, 32 or 64. */
+long long bchol_plan_task_count(int n, int k, int tile);
+bchol_status_t bchol_plan_task(int n, int k, int tile, long long ticket, int* type, int* s, int* I, int* J);
+
+/* Number of factor-kernel and solve-kernel launches made by the last call on
+ * this handle (for launch accounting). */
+int bchol_last_launch_count(bchol_handle_t handle);
+
+/* Library version string. */
+const char* bchol_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BCHOL_H */

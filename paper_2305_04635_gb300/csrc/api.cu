@@ -1,0 +1,237 @@
+// api.cu -- the C ABI of libbchol (declared in include/bchol.h): handle,
+// workspace management, argument checks and launches.
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/bchol.h"
+#include "bchol_internal.h"
+#include "schedule.cuh"
+
+namespace bchol {
+
+int num_sms() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) return 1;
+  return n;
+}
+
+// Workspace layout: [0, 256) status words (timeout record), then the region
+// used by one call (factor flags and control block, or inverted blocks).
+constexpr size_t kStatusBytes = 256;
+
+}  // namespace bchol
+
+struct bchol_handle_s {
+  cudaStream_t stream = nullptr;
+  void* ws_own = nullptr;
+  size_t ws_own_bytes = 0;
+  void* ws_lent = nullptr;
+  size_t ws_lent_bytes = 0;
+  int tile = 0;
+  int wait_ms = 2000;
+  int ctas_per_sm = 0;
+  int last_launches = 0;
+  int stall_I = -1, stall_J = -1;
+  int* last_status = nullptr;  // status word of the workspace used last
+};
+
+using namespace bchol;
+
+static int auto_tile(int k) {
+  if (k <= 128) return 16;
+  if (k <= 1024) return 32;
+  return 64;
+}
+
+static size_t call_bytes(bchol_handle_t h, int n, int k) {
+  const int kk = (n > 0 && k > n - 1) ? n - 1 : k;
+  const int b = h->tile ? h->tile : auto_tile(kk);
+  const FactorPlan P = make_factor_plan(n, kk, b);
+  size_t f = factor_workspace_bytes(P), s = solve_workspace_bytes(n, kk);
+  return kStatusBytes + (f > s ? f : s);
+}
+
+// Workspace of at least `bytes`: the lent buffer, or the handle's own one
+// (grown with cudaMalloc; its status words are zeroed when it is created).
+static bchol_status_t get_workspace(bchol_handle_t h, size_t bytes, char** ws) {
+  if (h->ws_lent) {
+    if (h->ws_lent_bytes < bytes) return BCHOL_ERR_ALLOC;
+    *ws = static_cast<char*>(h->ws_lent);
+    return BCHOL_OK;
+  }
+  if (h->ws_own_bytes < bytes) {
+    if (h->ws_own) {
+      if (cudaStreamSynchronize(h->stream) != cudaSuccess) return BCHOL_ERR_CUDA;
+      cudaFree(h->ws_own);
+      h->ws_own = nullptr;
+      h->ws_own_bytes = 0;
+      h->last_status = nullptr;
+    }
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return BCHOL_ERR_ALLOC;
+    }
+    if (cudaMemsetAsync(p, 0, kStatusBytes, h->stream) != cudaSuccess) {
+      cudaFree(p);
+      return BCHOL_ERR_CUDA;
+    }
+    h->ws_own = p;
+    h->ws_own_bytes = bytes;
+  }
+  *ws = static_cast<char*>(h->ws_own);
+  return BCHOL_OK;
+}
+
+extern "C" {
+
+bchol_status_t bchol_create(bchol_handle_t* handle, void* stream) {
+  if (!handle) return BCHOL_ERR_ARG;
+  bchol_handle_t h = new (std::nothrow) bchol_handle_s();
+  if (!h) return BCHOL_ERR_ALLOC;
+  h->stream = static_cast<cudaStream_t>(stream);
+  *handle = h;
+  return BCHOL_OK;
+}
+
+bchol_status_t bchol_destroy(bchol_handle_t h) {
+  if (!h) return BCHOL_ERR_ARG;
+  bchol_status_t rc = BCHOL_OK;
+  if (h->ws_own) {
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = BCHOL_ERR_CUDA;
+    cudaFree(h->ws_own);
+  }
+  delete h;
+  return rc;
+}
+
+bchol_status_t bchol_set_stream(bchol_handle_t h, void* stream) {
+  if (!h) return BCHOL_ERR_ARG;
+  h->stream = static_cast<cudaStream_t>(stream);
+  return BCHOL_OK;
+}
+
+bchol_status_t bchol_set_workspace(bchol_handle_t h, void* ptr, size_t bytes) {
+  if (!h) return BCHOL_ERR_ARG;
+  if (ptr == nullptr || bytes == 0) {
+    h->ws_lent = nullptr;
+    h->ws_lent_bytes = 0;
+    h->last_status = nullptr;
+    return BCHOL_OK;
+  }
+  if ((reinterpret_cast<uintptr_t>(ptr) & 15u) != 0 || bytes < kStatusBytes) return BCHOL_ERR_ARG;
+  if (cudaMemsetAsync(ptr, 0, kStatusBytes, h->stream) != cudaSuccess) return BCHOL_ERR_CUDA;
+  h->ws_lent = ptr;
+  h->ws_lent_bytes = bytes;
+  h->last_status = nullptr;
+  return BCHOL_OK;
+}
+
+size_t bchol_workspace_size(bchol_handle_t h, int n, int k) {
+  if (!h || n < 0 || k < 0) return 0;
+  return call_bytes(h, n, k);
+}
+
+bchol_status_t bchol_set_tile(bchol_handle_t h, int tile) {
+  if (!h || !(tile == 0 || tile == 16 || tile == 32 || tile == 64)) return BCHOL_ERR_ARG;
+  h->tile = tile;
+  return BCHOL_OK;
+}
+
+bchol_status_t bchol_set_wait_limit_ms(bchol_handle_t h, int ms) {
+  if (!h || ms < 1) return BCHOL_ERR_ARG;
+  h->wait_ms = ms;
+  return BCHOL_OK;
+}
+
+bchol_status_t bchol_set_ctas_per_sm(bchol_handle_t h, int c) {
+  if (!h || c < 0 || c > 32) return BCHOL_ERR_ARG;
+  h->ctas_per_sm = c;
+  return BCHOL_OK;
+}
+
+bchol_status_t bchol_set_stall_tile(bchol_handle_t h, int I, int J) {
+  if (!h || I < -1 || J < -1 || (I >= 0) != (J >= 0) || (I >= 0 && J > I)) return BCHOL_ERR_ARG;
+  h->stall_I = I;
+  h->stall_J = J;
+  return BCHOL_OK;
+}
+
+long long bchol_plan_task_count(int n, int k, int tile) {
+  if (n < 0 || k < 0 || !(tile == 16 || tile == 32 || tile == 64)) return -1;
+  return (long long)make_factor_plan(n, k, tile).total;
+}
+
+bchol_status_t bchol_plan_task(int n, int k, int tile, long long ticket, int* type, int* s, int* I, int* J) {
+  if (n < 0 || k < 0 || !(tile == 16 || tile == 32 || tile == 64) || !type || !s || !I || !J) return BCHOL_ERR_ARG;
+  const FactorPlan P = make_factor_plan(n, k, tile);
+  if (ticket < 0 || (unsigned long long)ticket >= P.total) return BCHOL_ERR_ARG;
+  decode_task(Schedule{P.S, P.p, P.Sreg, P.Treg}, ticket, *type, *s, *I, *J);
+  return BCHOL_OK;
+}
+
+int bchol_last_launch_count(bchol_handle_t h) { return h ? h->last_launches : 0; }
+
+const char* bchol_version(void) { return "bchol 0.1.0 (sm_103a)"; }
+
+bchol_status_t bchol_factor(bchol_handle_t h, int n, int k, double* ab, int ldab, int* info_dev) {
+  if (!h || n < 0 || k < 0 || ldab < k + 1 || !info_dev || (n > 0 && !ab)) return BCHOL_ERR_ARG;
+  h->last_launches = 0;
+  const int kk = (n > 0 && k > n - 1) ? n - 1 : k;
+  if (n == 0) return cudaMemsetAsync(info_dev, 0, sizeof(int), h->stream) == cudaSuccess ? BCHOL_OK : BCHOL_ERR_CUDA;
+  char* ws = nullptr;
+  bchol_status_t rc = get_workspace(h, call_bytes(h, n, k), &ws);
+  if (rc != BCHOL_OK) return rc;
+  const int b = h->tile ? h->tile : auto_tile(kk);
+  const FactorPlan P = make_factor_plan(n, kk, b);
+  int* status = reinterpret_cast<int*>(ws);
+  h->last_status = status;
+  cudaError_t e = launch_factor(P, ab, ldab, info_dev, ws + kStatusBytes, status,
+                                (uint64_t)h->wait_ms * 1000000ull, h->ctas_per_sm, h->stall_I, h->stall_J, h->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return BCHOL_ERR_CUDA;
+  }
+  h->last_launches = 1;
+  return BCHOL_OK;
+}
+
+bchol_status_t bchol_solve(bchol_handle_t h, int n, int k, int nrhs, const double* ab, int ldab, double* b,
+                           int ldb) {
+  if (!h || n < 0 || k < 0 || nrhs < 0 || ldab < k + 1 || ldb < (n > 1 ? n : 1)) return BCHOL_ERR_ARG;
+  if (n > 0 && nrhs > 0 && (!ab || !b)) return BCHOL_ERR_ARG;
+  h->last_launches = 0;
+  if (n == 0 || nrhs == 0) return BCHOL_OK;
+  char* ws = nullptr;
+  bchol_status_t rc = get_workspace(h, call_bytes(h, n, k), &ws);
+  if (rc != BCHOL_OK) return rc;
+  h->last_status = reinterpret_cast<int*>(ws);
+  int launches = 0;
+  cudaError_t e = launch_solve(n, k, nrhs, ab, ldab, b, ldb, ws + kStatusBytes, &launches, h->stream);
+  h->last_launches = launches;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return BCHOL_ERR_CUDA;
+  }
+  return BCHOL_OK;
+}
+
+bchol_status_t bchol_get_info(bchol_handle_t h, const int* info_dev, int count, int* info_host) {
+  if (!h || count < 0 || (count > 0 && (!info_dev || !info_host))) return BCHOL_ERR_ARG;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return BCHOL_ERR_CUDA;
+  if (count > 0 && cudaMemcpy(info_host, info_dev, sizeof(int) * (size_t)count, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return BCHOL_ERR_CUDA;
+  int status = 0;
+  if (h->last_status) {
+    if (cudaMemcpy(&status, h->last_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return BCHOL_ERR_CUDA;
+    if (status != 0 && cudaMemset(h->last_status, 0, sizeof(int)) != cudaSuccess) return BCHOL_ERR_CUDA;
+  }
+  if (status == kStatusTimeout) return BCHOL_ERR_TIMEOUT;
+  for (int i = 0; i < count; ++i)
+    if (info_host[i] > 0) return BCHOL_ERR_NOT_SPD;
+  return BCHOL_OK;
+}
+
+}  // extern "C"

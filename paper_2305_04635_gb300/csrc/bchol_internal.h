@@ -1,0 +1,41 @@
+// bchol_internal.h -- host-side declarations shared by the library's translation units.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bchol {
+
+// Values of the status word that records how the last launch ended.
+constexpr int kStatusOk = 0;
+constexpr int kStatusTimeout = 2;
+
+// Tile geometry of one factorization: S = ceil(n/b) tile rows, p = ceil(k/b)
+// sub-diagonal tiles per panel (clamped to S-1).
+struct FactorPlan {
+  int n = 0, k = 0, b = 32, S = 0, p = 0;
+  long long Sreg = 0;          // steps whose panel holds all p sub-diagonal tiles
+  long long Treg = 0;          // tasks per such step: 1 + p(p+3)/2
+  unsigned long long total = 0;  // tasks of the whole factorization
+  size_t flag_count = 0;       // ints of ready flags: S*(p+1)
+};
+
+FactorPlan make_factor_plan(int n, int k, int b);
+
+// Device workspace needed by one factorization (control block + flags).
+size_t factor_workspace_bytes(const FactorPlan& plan);
+
+// Launch the persistent factor kernel.  `ws` holds factor_workspace_bytes()
+// bytes; `status` is a device int that outlives the call (timeout record).
+cudaError_t launch_factor(const FactorPlan& plan, double* ab, long long ldab, int* info, void* ws, int* status,
+                          uint64_t wait_ns, int ctas_per_sm, int stall_I, int stall_J, cudaStream_t stream);
+
+// Solve: block size and workspace of the inverted diagonal blocks.
+int solve_block(int k);
+size_t solve_workspace_bytes(int n, int k);
+cudaError_t launch_solve(int n, int k, int nrhs, const double* ab, long long ldab, double* b, long long ldb,
+                         void* ws, int* launches, cudaStream_t stream);
+
+int num_sms();
+
+}  // namespace bchol

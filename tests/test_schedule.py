@@ -1,0 +1,55 @@
+"""The factor kernel's task order (host-side query of the same decode the kernel runs).
+
+Checks against the tiled algorithm of Sec. 3 (Algorithm 1 with the
+cross-iteration overlap): every task of every step appears exactly once, and
+every task comes after the tasks it depends on, so that a CTA only ever waits
+for smaller tickets (the walk cannot deadlock).
+"""
+import math
+
+import pytest
+
+import paper_2305_04635_gb300 as bchol
+
+
+def expected_tasks(n, k, b):
+    S = math.ceil(n / b)
+    kk = min(k, n - 1)
+    p = min(math.ceil(kk / b), S - 1)
+    tasks = set()
+    for s in range(S):
+        tasks.add((0, s, s, s))
+        for I in range(s + 1, min(S - 1, s + p) + 1):
+            tasks.add((1, s, I, s))
+            for J in range(s + 1, I + 1):
+                tasks.add((2, s, I, J))
+    return tasks, S, p
+
+
+@pytest.mark.parametrize("n,k,b", [(1, 0, 16), (10, 3, 16), (100, 31, 32), (100, 32, 32), (129, 64, 64),
+                                   (1000, 50, 16), (500, 0, 32), (50, 60, 16), (3000, 130, 32), (777, 200, 64),
+                                   (640, 639, 64)])
+def test_schedule_is_complete_and_topological(n, k, b):
+    got = bchol.plan_tasks(n, k, b)
+    want, S, p = expected_tasks(n, k, b)
+    assert len(got) == len(set(got)) == len(want)
+    assert set(got) == want
+    ticket = {t: i for i, t in enumerate(got)}
+    done_steps = {}   # tile (I, J) -> steps whose update precedes in ticket order
+    for i, (typ, s, I, J) in enumerate(got):
+        if typ == 0:
+            deps = [(2, s - 1, s, s)] if s >= 1 and s - 1 >= max(0, s - p) else []
+        elif typ == 1:
+            deps = [(0, s, s, s)] + ([(2, s - 1, I, s)] if s - 1 >= max(0, I - p) else [])
+        else:
+            deps = [(1, s, I, s), (1, s, J, s)] + ([(2, s - 1, I, J)] if s - 1 >= max(0, I - p) else [])
+        for d in deps:
+            assert d in ticket and ticket[d] < i, (d, (typ, s, I, J))
+
+
+def test_task_count_matches_closed_form():
+    for n, k, b in [(100000, 2000, 64), (100000, 500, 32), (100000, 50, 16)]:
+        S = math.ceil(n / b)
+        p = math.ceil(k / b)
+        total = (S - p) * (1 + p * (p + 3) // 2) + sum(1 + m * (m + 3) // 2 for m in range(p))
+        assert bchol.load_library().bchol_plan_task_count(n, k, b) == total
