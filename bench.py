@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Benchmark of the FP64 band Cholesky factor + solve on one GB300.
+
+Workload (the plain FP64 sweep): single SPD band matrices of order
+n = 100000 with half-bandwidth k in {50, 100, 200, 500, 1000, 2000}, A = L0 L0^T
+with L0 lower banded, off-diagonals U(-1,1)/sqrt(k), diagonal log-uniform in
+[1, 1e3], seed 0, one right-hand side b ~ N(0,1).  One step factors and
+solves every matrix of the sweep once.  Inputs are synthetic, generated by
+bandgen; the band (k+1 x n) is restored from a pristine device copy and L2
+is flushed (a 256 MB write) before each factorization.
+
+value  = sum over k of the Eq. (1) flop count F(n,k) / (wall time of one step)
+         (the paper's GFLOP/s convention, Sec. 3.2 and Table 1).
+e2e    = the same metric when every step also copies A and b from pinned
+         host memory and reads x and info back (the public Python API).
+roofline = the factor kernel: achieved n*k^2 flops per second (CUDA events
+         around each factor launch) against the FP64 peak.
+cpu_baseline = the serial CPU oracle on a leading block of each matrix,
+         extrapolated by F(n,k)/F(n',k).
+
+Multi-GPU: replicas only (one independent sweep per rank); value sums the
+ranks' flops over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+import bandgen  # noqa: E402
+from paper_2305_04635_gb300.flops import band_bytes, flops_eq1, flops_nk2  # noqa: E402
+
+METRIC = "banded Cholesky GFLOP/s and % roofline over n,k; batched/adjoint vs plain"
+N_ROWS = 100000
+KS = [50, 100, 200, 500, 1000, 2000]
+# FP64 peak: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (the nominal 1.25 TFLOP/s).
+FP64_PEAK_TFLOPS = 1.25
+HBM_FALLBACK_GBS = 6800.0
+L2_FLUSH_BYTES = 256 << 20
+
+
+def measured_hbm_gbs() -> tuple[float, str]:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def roofline_ms(n: int, k: int, hbm_gbs: float) -> float:
+    t_flop = flops_nk2(n, k) / (FP64_PEAK_TFLOPS * 1e12)
+    t_mem = 2 * band_bytes(n, k) / (hbm_gbs * 1e9)
+    return 1e3 * max(t_flop, t_mem)
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.idx = device_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(n: int, ks: list[int]):
+    data = {}
+    for k in ks:
+        L0 = bandgen.l0_band(n, k, seed=0, diag="log1e3")
+        A = bandgen.band_product(L0, k)
+        B = bandgen.rhs(n, 1, seed=0)[:, 0].copy()
+        data[k] = (A, B)
+    return data
+
+
+def run_ours(args, rank: int, world: int, dev: int):
+    import paper_2305_04635_gb300 as bchol
+
+    torch.cuda.set_device(dev)
+    ks = args.ks
+    n = args.n
+    data = make_inputs(n, ks)
+    stream = torch.cuda.current_stream()
+    h = bchol.Handle()
+    bufs = {}
+    for k in ks:
+        A, B = data[k]
+        pristine = bchol.band_from_numpy(A)
+        work = bchol.band_from_numpy(A)
+        host_A = torch.from_numpy(np.ascontiguousarray(A.T)).pin_memory()   # (n, k+1) == band, column-major
+        host_b = torch.from_numpy(B).pin_memory()
+        host_x = torch.empty(n, dtype=torch.float64).pin_memory()
+        host_info = torch.empty(1, dtype=torch.int32).pin_memory()
+        b_pr = torch.from_numpy(B).cuda()
+        bufs[k] = dict(pristine=pristine, work=work, b_pr=b_pr, b=b_pr.clone(), info=torch.zeros(1, dtype=torch.int32,
+                       device="cuda"), host_A=host_A, host_b=host_b, host_x=host_x, host_info=host_info)
+    flush = torch.empty(L2_FLUSH_BYTES // 8, dtype=torch.float64, device="cuda")
+    ev = {k: [torch.cuda.Event(enable_timing=True) for _ in range(3)] for k in ks}
+    fac_ms = {k: [] for k in ks}
+    sol_ms = {k: [] for k in ks}
+
+    def step(record: bool):
+        for k in ks:
+            bb = bufs[k]
+            bb["work"].copy_(bb["pristine"])
+            bb["b"].copy_(bb["b_pr"])
+            flush.fill_(1.0)
+            e0, e1, e2 = ev[k]
+            e0.record(stream)
+            bchol.factor(bb["work"], k, info=bb["info"], handle=h)
+            e1.record(stream)
+            bchol.solve(bb["work"], k, bb["b"], handle=h)
+            e2.record(stream)
+        torch.cuda.synchronize()
+        if record:
+            for k in ks:
+                e0, e1, e2 = ev[k]
+                fac_ms[k].append(e0.elapsed_time(e1))
+                sol_ms[k].append(e1.elapsed_time(e2))
+
+    def e2e_step():
+        for k in ks:
+            bb = bufs[k]
+            bb["work"].T.copy_(bb["host_A"], non_blocking=True)
+            bb["b"].copy_(bb["host_b"], non_blocking=True)
+            bchol.factor(bb["work"], k, info=bb["info"], handle=h)
+            bchol.solve(bb["work"], k, bb["b"], handle=h)
+            bb["host_x"].copy_(bb["b"], non_blocking=True)
+            bb["host_info"].copy_(bb["info"], non_blocking=True)
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step(False)
+    # correctness gate on the last warm-up results
+    for k in ks:
+        rc, infos = bchol.get_info(bufs[k]["info"], handle=h)
+        if rc != 0 or infos[0] != 0:
+            raise RuntimeError(f"factorization failed for k={k}: status {rc}, info {infos}")
+
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step(True)
+    torch.cuda.synchronize()
+    barrier(world)
+    t1 = time.perf_counter()
+    clk = clocks.stop()
+    wall = t1 - t0
+
+    # end-to-end through the public API with host buffers
+    for _ in range(1):
+        e2e_step()
+    barrier(world)
+    torch.cuda.synchronize()
+    te0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    te1 = time.perf_counter()
+    for k in ks:
+        if int(bufs[k]["host_info"][0]) != 0:
+            raise RuntimeError(f"e2e factorization failed for k={k}")
+    wall_e2e = te1 - te0
+
+    walls = gather_max(world, [wall, wall_e2e])
+    wall, wall_e2e = walls
+    F = sum(flops_eq1(n, k) for k in ks)
+    value = world * F * args.steps / wall / 1e9
+    e2e_value = world * F * args.steps / wall_e2e / 1e9
+
+    hbm, hbm_kind = measured_hbm_gbs()
+    per_k = {}
+    tot_flop, tot_ms = 0.0, 0.0
+    for k in ks:
+        fm = statistics.median(fac_ms[k])
+        sm = statistics.median(sol_ms[k])
+        roof = roofline_ms(n, k, hbm)
+        per_k[str(k)] = {"factor_ms": round(fm, 4), "solve_ms": round(sm, 4),
+                         "factor_gflops_eq1": round(flops_eq1(n, k) / fm / 1e6, 2),
+                         "factor_gflops_nk2": round(flops_nk2(n, k) / fm / 1e6, 2),
+                         "frac_fp64_roofline": round(roof / fm, 4)}
+        tot_flop += flops_nk2(n, k) * len(fac_ms[k])
+        tot_ms += sum(fac_ms[k])
+    achieved_tflops = tot_flop / (tot_ms * 1e-3) / 1e12
+    ms_per_step = 1e3 * wall / args.steps
+    launches_per_step = 3 * len(ks)   # factor kernel + inverse-block kernel + solve kernel per matrix
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"plain FP64 sweep: n={n}, k in {ks}, L0 diag log-uniform [1,1e3], 1 RHS, "
+                               "factor + solve per matrix", "n": n, "k": ks, "nrhs": 1,
+                   "l2": "256 MB flush write before every factorization (inputs for k <= 100 are below L2 size)",
+                   "parallelism": f"replicas x{world}"},
+        "per_k": per_k,
+        "e2e": {"value": round(e2e_value, 3), "unit": "GFLOP/s",
+                "h2d_bytes_per_step": sum(8 * (k + 1) * n + 8 * n for k in ks),
+                "d2h_bytes_per_step": sum(8 * n + 4 for k in ks)},
+        "roofline": {"bound": "alu", "achieved": round(achieved_tflops, 4), "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": round(achieved_tflops / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                     "kernel": "factor_kernel", "flops_per_launch": "n*k^2",
+                     "peak_source": "FP64 nominal from unit counts and clock (alu)"},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+    }
+    return out, data
+
+
+def cpu_baseline(n: int, ks: list[int], data=None, budget_s: float = 20.0) -> dict:
+    """The oracle as it stands on a leading block of each matrix (serial, one core)."""
+    import oracle
+
+    oracle.build()
+    total_f, total_t = 0.0, 0.0
+    samples = []
+    per_k_budget = budget_s / len(ks)
+    for k in ks:
+        # n' rows take about per_k_budget seconds at the oracle's ~0.6 GFLOP/s; at least 2k rows
+        nprime = int(min(n, max(2 * k, per_k_budget * 0.6e9 / max(1, (k + 1) * (k + 4)))))
+        L0 = bandgen.l0_band(nprime, k, seed=0, diag="log1e3")
+        A = bandgen.band_product(L0, k)
+        B = bandgen.rhs(nprime, 1, seed=0)[:, 0]
+        t0 = time.perf_counter()
+        L, info = oracle.pbtrf(A, k)
+        oracle.pbtrs(L, k, B)
+        dt = time.perf_counter() - t0
+        scale = flops_eq1(n, k) / flops_eq1(nprime, k)
+        total_f += flops_eq1(n, k)
+        total_t += dt * scale
+        samples.append(f"k={k}: n'={nprime}")
+    return {"value": round(total_f / total_t / 1e9, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+            "sample": "factor+solve of the leading n' rows of each matrix, time scaled by F(n,k)/F(n',k): "
+                      + ", ".join(samples)}
+
+
+def barrier(world: int):
+    if world > 1:
+        torch.distributed.barrier()
+
+
+def gather_max(world: int, vals: list[float]) -> list[float]:
+    if world == 1:
+        return vals
+    t = torch.tensor(vals, dtype=torch.float64, device="cuda")
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return t.tolist()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_ROWS)
+    ap.add_argument("--ks", type=lambda s: [int(x) for x in s.split(",")], default=KS)
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        # The reference arm is the CPU oracle itself (the paper ships no runnable code).
+        if rank != 0:
+            return
+        steps_t = []
+        base = None
+        for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            base = cpu_baseline(args.n, args.ks, budget_s=max(2.0, args.cpu_budget / max(1, args.steps)))
+            if i >= args.warmup:
+                steps_t.append(time.perf_counter() - t0)
+        out = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": "GFLOP/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.median(steps_t), 3),
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic",
+               "config": {"workload": f"plain FP64 sweep: n={args.n}, k in {args.ks}, L0 diag log-uniform [1,1e3], "
+                                      "1 RHS, factor + solve per matrix", "n": args.n, "k": args.ks, "nrhs": 1},
+               "cpu_baseline": base,
+               "e2e": {"value": base["value"], "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return
+
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    out, data = run_ours(args, rank, world, local)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(args.n, args.ks, budget_s=args.cpu_budget)
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
