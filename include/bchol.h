@@ -87,6 +87,29 @@ size_t bchol_workspace_size(bchol_handle_t handle, int n, int k);
 bchol_status_t bchol_factor(bchol_handle_t handle, int n, int k, double* ab, int ldab, int* info_dev);
 
 /*
+ * bchol_factor_noalloc -- bchol_factor for callers that may not allocate GPU
+ * memory.  The paper has no counterpart: this exists for code that must not
+ * call cudaMalloc, such as allocators or arenas that own all device memory,
+ * real-time hosts that forbid allocation after start-up, or plugins whose
+ * host application owns every allocation.  It takes no handle and allocates
+ * nothing.  The factor kernel's scratch (task ticket, abort word, per-tile
+ * ready flags) lives in one fixed 1 MiB array in the library's device memory,
+ * which every GPU that loads the library holds until the process exits.
+ *   stream      cudaStream_t to launch on (NULL = legacy default stream)
+ *   n, k, ab, ldab, info_dev   as for bchol_factor (same kernel, same results)
+ *   status_dev  device int owned by the caller: set to 0, then to
+ *               BCHOL_ERR_TIMEOUT (2) if a bounded in-kernel wait ran out
+ * Returns BCHOL_ERR_UNSUPPORTED, with nothing launched, when the problem needs
+ * more scratch than the array holds (about 262000 tile ready flags: n = 1e5
+ * with k up to a few thousand fits).  All calls on a device share the array,
+ * so calls that overlap on the GPU race; order them.  The first call on each
+ * device looks up the array's device address; make it before any stream
+ * capture.
+ */
+bchol_status_t bchol_factor_noalloc(void* stream, int n, int k, double* ab, int ldab, int* info_dev,
+                                    int* status_dev);
+
+/*
  * bchol_solve -- X = A^{-1} B from the factor that bchol_factor left in ab
  * (LAPACK pbtrs semantics, lower): L Y = B by forward substitution, then
  * L^T X = Y by back substitution.  The paper solves no systems itself; its
