@@ -2,17 +2,21 @@
 // semantics): forward substitution L Y = B, then back substitution L^T X = Y.
 // The paper factors only; the solve is the use it motivates (Sec. 1, Sec. 2).
 //
-// Rows are taken in blocks of 32.  With y_I the I-th block of Y,
-//     y_I = L_II^{-1} (b_I - sum_{J=I-P}^{I-1} L_IJ y_J),     P = ceil(k/32),
-//     x_I = L_II^{-T} (y_I - sum_{J=I+1}^{I+P} L_JI^T x_J).
-// The chain over I is sequential.  To keep it short, the diagonal blocks are
-// inverted first, all at once (inv_diag_kernel), so each chain step is two
-// small matrix-vector products instead of a 32-step substitution.  The sweep
-// runs on one thread-block cluster: CTA 0 (the leader) owns the chain and the
-// nearest block L_{I,I-1}; the other CTAs compute the far contributions
-// (J <= I-2) one block ahead and write their partial sums straight into the
-// leader's shared memory (distributed shared memory).  One cluster barrier
-// separates two chain steps.
+// Rows are taken in blocks of 32.  With P = ceil(k/32) and blocks y_I, x_I:
+//     y_I = L_II^{-1} b_I - M_I y_{I-1} - L_II^{-1} sum_{J=I-P}^{I-2} L_IJ y_J,   M_I = L_II^{-1} L_{I,I-1}
+//     x_I = L_II^{-T} y_I - N_I x_{I+1} - L_II^{-T} sum_{J=I+2}^{I+P} L_JI^T x_J, N_I = (L_{I+1,I} L_II^{-1})^T
+// solve_prep_kernel forms L_II^{-1}, M_I and N_I for all blocks at once.
+// The sequential chain then costs one 32 x 32 matrix-vector product per block.
+//
+// The sweeps run on one thread-block cluster (16 CTAs, or 8 when 16 cannot
+// be scheduled).  CTA 0, the leader, runs the chain.  The other CTAs (the
+// workers) own the far blocks J = w-1 (mod CL-1).  One round ahead of the
+// leader they form their share L_II^{-1} sum_J L_IJ y_J (worker 1 also folds
+// in the L_II^{-1} b_I term) and write it into the leader's shared memory.
+// The leader pushes each new block y_I into the shared memory of the worker
+// that owns block I.  The workers prefetch next round's band tiles into
+// registers, so no global-memory latency sits on the chain.  One cluster
+// barrier separates two rounds.
 #include <cooperative_groups.h>
 
 #include "bchol_device.cuh"
@@ -26,42 +30,90 @@ constexpr int kSB = 32;        // solve block
 constexpr int kNRC = 8;        // right-hand sides per pass
 constexpr int kSThreads = 256;
 constexpr int kSWarps = kSThreads / 32;
+constexpr int kQ = kSB / kSWarps;   // columns per warp in a 32 x 32 product
+constexpr int kMaxT = 6;            // far tiles per worker per round prefetched into shared memory
+constexpr int kRing = kMaxT + 1;    // pushed solution blocks kept per worker
+constexpr size_t kBlk = (size_t)kSB * kSB;
 
 int solve_block(int) { return kSB; }
 
 size_t solve_workspace_bytes(int n, int) {
   const size_t S = (size_t)((n + kSB - 1) / kSB);
-  return S * kSB * kSB * sizeof(double);
+  return 3 * S * kBlk * sizeof(double);
 }
 
-// L_II^{-1} of every diagonal block, column-major per block.  Thread c forms
-// column c by forward substitution on the unit vector e_c.  Rows past n are
-// padded with the identity.
-__global__ void __launch_bounds__(32) inv_diag_kernel(const double* __restrict__ ab, long long ldab, int n, int k,
-                                                      double* __restrict__ linv) {
-  __shared__ double sL[kSB * kSB];
+// Band entry L(gi, gj) (zero outside the band or the matrix).
+__device__ __forceinline__ double lband(const double* __restrict__ ab, long long ldab, int n, int k, int gi, int gj) {
+  const int d = gi - gj;
+  return (gi < n && gj >= 0 && d >= 0 && d <= k) ? __ldg(ab + d + (long long)gj * ldab) : 0.0;
+}
+
+// Per block I: L_II^{-1}, M_I = L_II^{-1} L_{I,I-1} and N_I = (L_{I+1,I} L_II^{-1})^T,
+// each 32 x 32 column-major.  Rows past n are padded with the identity.
+__global__ void __launch_bounds__(256) solve_prep_kernel(const double* __restrict__ ab, long long ldab, int n, int k,
+                                                         int S, double* __restrict__ linv, double* __restrict__ mfw,
+                                                         double* __restrict__ nbw) {
+  __shared__ double sL[kSB][kSB + 1];
+  __shared__ double sInv[kSB][kSB + 1];
+  __shared__ double sC[kSB][kSB + 1];
   __shared__ double rinv[kSB];
-  const int I = blockIdx.x, c = threadIdx.x;
-  const int gi = I * kSB + c;
-#pragma unroll 4
-  for (int j = 0; j < kSB; ++j) {
-    const int gj = I * kSB + j, d = gi - gj;
-    sL[j * kSB + c] = (gi < n && d >= 0 && d <= k) ? ab[d + (long long)gj * ldab] : 0.0;
+  const int I = blockIdx.x, tid = threadIdx.x;
+  for (int idx = tid; idx < kSB * kSB; idx += 256) {
+    const int i = idx % kSB, j = idx / kSB;
+    const int gi = I * kSB + i, gj = I * kSB + j;
+    double v = lband(ab, ldab, n, k, gi, gj);
+    if (gi >= n && i == j) v = 1.0;
+    sL[i][j] = v;
   }
-  __syncwarp();
-  rinv[c] = (gi < n) ? 1.0 / sL[c * kSB + c] : 1.0;
-  __syncwarp();
-  double x[kSB];
+  __syncthreads();
+  if (tid < kSB) rinv[tid] = 1.0 / sL[tid][tid];
+  __syncthreads();
+  if (tid < kSB) {
+    // column c of L^{-1} by forward substitution on e_c
+    const int c = tid;
+    double x[kSB];
 #pragma unroll
-  for (int i = 0; i < kSB; ++i) {
-    double s = 0.0;
+    for (int i = 0; i < kSB; ++i) {
+      double s = 0.0;
 #pragma unroll
-    for (int l = 0; l < i; ++l) s = fma(sL[l * kSB + i], x[l], s);
-    x[i] = (i < c) ? 0.0 : ((i == c) ? rinv[i] : -s * rinv[i]);
+      for (int l = 0; l < i; ++l) s = fma(sL[i][l], x[l], s);
+      x[i] = (i < c) ? 0.0 : ((i == c) ? rinv[i] : -s * rinv[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < kSB; ++i) sInv[i][c] = x[i];
   }
-  double* out = linv + (size_t)I * kSB * kSB + (size_t)c * kSB;
-#pragma unroll
-  for (int i = 0; i < kSB; ++i) out[i] = x[i];
+  __syncthreads();
+  double* li = linv + (size_t)I * kBlk;
+  for (int idx = tid; idx < kSB * kSB; idx += 256) li[idx] = sInv[idx % kSB][idx / kSB];
+  if (I >= 1) {
+    for (int idx = tid; idx < kSB * kSB; idx += 256) {
+      const int i = idx % kSB, j = idx / kSB;
+      sC[i][j] = lband(ab, ldab, n, k, I * kSB + i, (I - 1) * kSB + j);
+    }
+    __syncthreads();
+    double* m = mfw + (size_t)I * kBlk;
+    for (int idx = tid; idx < kSB * kSB; idx += 256) {
+      const int i = idx % kSB, j = idx / kSB;
+      double s = 0.0;
+      for (int l = 0; l <= i; ++l) s = fma(sInv[i][l], sC[l][j], s);
+      m[j * kSB + i] = s;
+    }
+    __syncthreads();
+  }
+  if (I + 1 < S) {
+    for (int idx = tid; idx < kSB * kSB; idx += 256) {
+      const int l = idx % kSB, m = idx / kSB;
+      sC[l][m] = lband(ab, ldab, n, k, (I + 1) * kSB + l, I * kSB + m);
+    }
+    __syncthreads();
+    double* nb = nbw + (size_t)I * kBlk;
+    for (int idx = tid; idx < kSB * kSB; idx += 256) {
+      const int l = idx % kSB, i = idx / kSB;     // G = L_{I+1,I} L_II^{-1}; N(i,l) = G(l,i) at [l*32+i]
+      double s = 0.0;
+      for (int m = i; m < kSB; ++m) s = fma(sC[l][m], sInv[m][i], s);
+      nb[l * kSB + i] = s;
+    }
+  }
 }
 
 struct SolveArgs {
@@ -72,126 +124,214 @@ struct SolveArgs {
   long long ldb;
   int nrhs;
   const double* linv;
+  const double* mfw;
+  const double* nbw;
+  int use_ring;   // far solution blocks come from the pushed ring (else from global memory)
 };
 
-// Band entry L(gi, gj) (zero outside the band or the matrix).
-__device__ __forceinline__ double lband(const SolveArgs& a, int gi, int gj) {
-  const int d = gi - gj;
-  return (gi < a.n && gj >= 0 && d >= 0 && d <= a.k) ? __ldg(a.ab + d + (long long)gj * a.ldab) : 0.0;
+// Shared-memory layout (doubles).  The leader and the workers use different
+// parts of the union.  pfs/lvs are per-thread prefetch slots, double-buffered
+// by chain position, filled with cp.async: unlike plain loads, these copies do
+// not hold up the release of the cluster barrier at the end of a round.
+template <int NW>
+struct SolveSmem {
+  union {
+    double part[2][NW][kNRC][kSB];        // leader: workers' shares for the next two blocks
+    struct {
+      double pfs[2][kMaxT][kQ][kSThreads];  // worker: far band tiles
+      double ring[kRing][kNRC][kSB];        // worker: solution blocks pushed by the leader
+    } w;
+  } u;
+  double lvs[2][kQ][kSThreads];           // L_TT^{-1} (worker) or M_T / N_T (leader)
+  double red[kSWarps][kNRC][kSB];
+  double vec[kNRC][kSB];                  // leader: last chain block; worker: its partial sum
+};
+
+__device__ __forceinline__ void cp_async8(double* dst, const double* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int sz = valid ? 8 : 0;   // 0: nothing is read and the slot is zero-filled
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(sz) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Balanced-tree sum of N values p[0], p[stride], ... (short dependency chains).
+template <int N>
+__device__ __forceinline__ double tree_sum(const double* p, int stride) {
+  if constexpr (N == 1) {
+    return p[0];
+  } else {
+    constexpr int H = N / 2;
+    return tree_sum<H>(p, stride) + tree_sum<N - H>(p + H * stride, stride);
+  }
 }
 
-// acc[rhs] += sum over this warp's columns l = w, w+8, .. of M(i, l) v[rhs][l]
-// then reduce the warps' sums through shared memory into out[rhs][i].
-__device__ __forceinline__ void reduce_rows(double (&acc)[kNRC], double* red, int nr, double* out) {
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+// Cross-warp sum: each warp's per-lane values acc[r] (r < nr) -> out[r][lane] (32*nr threads write).
+template <int NW>
+__device__ __forceinline__ void warp_sum_rows(const double (&acc)[kNRC], int nr, SolveSmem<NW>& sm, int w, int lane) {
 #pragma unroll
-  for (int r = 0; r < kNRC; ++r) red[(w * kNRC + r) * kSB + lane] = acc[r];
+  for (int r = 0; r < kNRC; ++r)
+    if (r < nr) sm.red[w][r][lane] = acc[r];
   __syncthreads();
-  if (tid < nr * kSB) {
-    const int r = tid / kSB, i = tid % kSB;
-    double s = 0.0;
-#pragma unroll
-    for (int ww = 0; ww < kSWarps; ++ww) s += red[(ww * kNRC + r) * kSB + i];
-    out[r * kSB + i] = s;
-  }
-  __syncthreads();
+}
+
+// Band tile entry for the 32 x 32 products of the sweeps, laid out so that lane = output row i
+// and column c = w + 8q: forward uses L_TJ(i, c), backward uses L_JT(c, i) (the transpose).
+__device__ __forceinline__ double tile_entry(const SolveArgs& a, bool fwd, int T, int J, int i, int c) {
+  return fwd ? lband(a.ab, a.ldab, a.n, a.k, T * kSB + i, J * kSB + c)
+             : lband(a.ab, a.ldab, a.n, a.k, J * kSB + c, T * kSB + i);
+}
+
+// Address and validity of the same entry, for cp.async.
+__device__ __forceinline__ const double* tile_addr(const SolveArgs& a, bool fwd, int T, int J, int i, int c, bool* ok) {
+  const int gi = fwd ? T * kSB + i : J * kSB + c;   // row
+  const int gj = fwd ? J * kSB + c : T * kSB + i;   // column
+  const int d = gi - gj;
+  *ok = (gi < a.n && gj >= 0 && d >= 0 && d <= a.k);
+  return *ok ? a.ab + d + (long long)gj * a.ldab : a.ab;
 }
 
 template <int CL>
 __global__ void __launch_bounds__(kSThreads, 1) solve_kernel(SolveArgs a) {
   constexpr int NW = CL - 1;
-  extern __shared__ __align__(16) double smem[];
-  double* part = smem;                          // [2][NW][kNRC][kSB], written by the workers
-  double* red = part + 2 * NW * kNRC * kSB;     // [kSWarps][kNRC][kSB]
-  double* tmp = red + kSWarps * kNRC * kSB;     // [kNRC][kSB]
-  double* ycur = tmp + kNRC * kSB;              // [kNRC][kSB]: the last block of the chain
-  double* sum = ycur + kNRC * kSB;              // [kNRC][kSB]
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SolveSmem<NW>& sm = *reinterpret_cast<SolveSmem<NW>*>(smem_raw);
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
-  double* part_leader = cluster.map_shared_rank(part, 0);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  SolveSmem<NW>* leader = cluster.map_shared_rank(&sm, 0);
 
   for (int c0 = 0; c0 < a.nrhs; c0 += kNRC) {
     const int nr = min(kNRC, a.nrhs - c0);
     double* bc = a.b + (long long)c0 * a.ldb;
     for (int sweep = 0; sweep < 2; ++sweep) {
       const bool fwd = (sweep == 0);
-      if (rank == 0)
-        for (int idx = tid; idx < 2 * NW * kNRC * kSB; idx += kSThreads) part[idx] = 0.0;
-      cluster.sync();
-      for (int step = 0; step < a.S; ++step) {
-        const int I = fwd ? step : a.S - 1 - step;
+      for (int idx = tid; idx < kNRC * kSB; idx += kSThreads) (&sm.vec[0][0])[idx] = 0.0;
+      // Registers prefetched one round ahead: the worker's far tiles and L_TT^{-1} (or its
+      // transpose), or the leader's coupling block M_T / N_T.  Lane = output row i, column
+      // c = w + 8q of the 32 x 32 product.
+      auto prefetch = [&](int pos) {
+        if (pos >= a.S) return;
+        const int T = fwd ? pos : a.S - 1 - pos;
+        const int buf = pos & 1;
         if (rank == 0) {
-          // near block: L_{I,I-1} y_{I-1} (forward) or L_{I+1,I}^T x_{I+1} (backward)
-          double acc[kNRC];
+          const bool has = fwd ? (T >= 1) : (T + 1 < a.S);
+          const double* cb = (fwd ? a.mfw : a.nbw) + (size_t)T * kBlk;
 #pragma unroll
-          for (int r = 0; r < kNRC; ++r) acc[r] = 0.0;
-          const int Jn = fwd ? I - 1 : I + 1;
-          if (Jn >= 0 && Jn < a.S) {
+          for (int q = 0; q < kQ; ++q) cp_async8(&sm.lvs[buf][q][tid], has ? cb + (w + kSWarps * q) * kSB + lane : a.ab, has);
+          cp_async_commit();
+          return;
+        }
+        const double* li = a.linv + (size_t)T * kBlk;
 #pragma unroll
-            for (int q = 0; q < kSB / kSWarps; ++q) {
-              const int l = w + kSWarps * q;
-              const double m = fwd ? lband(a, I * kSB + lane, Jn * kSB + l) : lband(a, Jn * kSB + l, I * kSB + lane);
+        for (int q = 0; q < kQ; ++q) {
+          const int c = w + kSWarps * q;   // forward: Linv(i, c) at [c*32+i]; backward: Linv(c, i) at [i*32+c]
+          cp_async8(&sm.lvs[buf][q][tid], li + (fwd ? c * kSB + lane : lane * kSB + c), true);
+        }
+        const int jlo = fwd ? max(0, T - a.P) : T + 2;
+        const int jhi = fwd ? T - 2 : min(a.S - 1, T + a.P);
+        int J = jlo + ((rank - 1) - (jlo % NW) + NW) % NW;
+        for (int t = 0; t < kMaxT && J <= jhi; ++t, J += NW) {
 #pragma unroll
-              for (int r = 0; r < kNRC; ++r) acc[r] = fma(m, ycur[r * kSB + l], acc[r]);
-            }
+          for (int q = 0; q < kQ; ++q) {
+            bool ok;
+            const double* src = tile_addr(a, fwd, T, J, lane, w + kSWarps * q, &ok);
+            cp_async8(&sm.u.w.pfs[buf][t][q][tid], src, ok);
           }
-          reduce_rows(acc, red, nr, sum);
-          if (tid < nr * kSB) {
-            const int r = tid / kSB, i = tid % kSB, gi = I * kSB + i;
-            double v = (gi < a.n) ? bc[gi + (long long)r * a.ldb] : 0.0;
-            v -= sum[r * kSB + i];
-            const double* pp = part + (size_t)(I & 1) * NW * kNRC * kSB;
-#pragma unroll 1
-            for (int ww = 0; ww < NW; ++ww) v -= pp[(ww * kNRC + r) * kSB + i];
-            tmp[r * kSB + i] = v;
-          }
-          __syncthreads();
-          // y_I = L_II^{-1} tmp   or   x_I = L_II^{-T} tmp
-          const double* li = a.linv + (size_t)I * kSB * kSB;
+        }
+        cp_async_commit();
+      };
+      // Worker: its share of chain block T (at position pos), into the leader's part slot:
+      //   forward  L_TT^{-1} (sum_J L_TJ y_J  [- b_T for worker 1])
+      //   backward L_TT^{-T} (sum_J L_JT^T x_J [- y_T for worker 1])
+      auto worker_step = [&](int pos) {
+        const int T = fwd ? pos : a.S - 1 - pos;
+        const int jlo = fwd ? max(0, T - a.P) : T + 2;
+        const int jhi = fwd ? T - 2 : min(a.S - 1, T + a.P);
+        double acc[kNRC];
 #pragma unroll
-          for (int r = 0; r < kNRC; ++r) acc[r] = 0.0;
+        for (int r = 0; r < kNRC; ++r) acc[r] = 0.0;
+        const int buf = pos & 1;
+        cp_async_wait_all();
+        int J = jlo + ((rank - 1) - (jlo % NW) + NW) % NW;
+        for (int t = 0; J <= jhi; ++t, J += NW) {
+          const double* ring = &sm.u.w.ring[(J / NW) % kRing][0][0];
 #pragma unroll
-          for (int q = 0; q < kSB / kSWarps; ++q) {
-            const int l = w + kSWarps * q;
-            const double m = fwd ? li[l * kSB + lane] : li[lane * kSB + l];
+          for (int q = 0; q < kQ; ++q) {
+            const int c = w + kSWarps * q;
+            const double m = (t < kMaxT) ? sm.u.w.pfs[buf][t][q][tid] : tile_entry(a, fwd, T, J, lane, c);
+            const int gc = J * kSB + c;
 #pragma unroll
-            for (int r = 0; r < kNRC; ++r) acc[r] = fma(m, tmp[r * kSB + l], acc[r]);
-          }
-          reduce_rows(acc, red, nr, ycur);
-          if (tid < nr * kSB) {
-            const int r = tid / kSB, i = tid % kSB, gi = I * kSB + i;
-            if (gi < a.n) bc[gi + (long long)r * a.ldb] = ycur[r * kSB + i];
-          }
-        } else {
-          // far blocks of the next chain step, this worker's share
-          const int T = fwd ? I + 1 : I - 1;
-          if (T >= 0 && T < a.S) {
-            double acc[kNRC];
-#pragma unroll
-            for (int r = 0; r < kNRC; ++r) acc[r] = 0.0;
-            const int jlo = fwd ? max(0, T - a.P) : T + 2;
-            const int jhi = fwd ? T - 2 : min(a.S - 1, T + a.P);
-            int j0 = jlo + ((rank - 1) - (jlo % NW) + NW) % NW;
-            for (int J = j0; J <= jhi; J += NW) {
-#pragma unroll
-              for (int q = 0; q < kSB / kSWarps; ++q) {
-                const int l = w + kSWarps * q;
-                const int gl = J * kSB + l;
-                const double m = fwd ? lband(a, T * kSB + lane, gl) : lband(a, gl, T * kSB + lane);
-                if (gl < a.n) {
-#pragma unroll
-                  for (int r = 0; r < kNRC; ++r)
-                    if (r < nr) acc[r] = fma(m, __ldcg(bc + gl + (long long)r * a.ldb), acc[r]);
-                }
+            for (int r = 0; r < kNRC; ++r) {
+              if (r < nr) {
+                const double v = a.use_ring ? ring[r * kSB + c]
+                                            : (gc < a.n ? __ldcg(bc + gc + (long long)r * a.ldb) : 0.0);
+                acc[r] = fma(m, v, acc[r]);
               }
             }
-            reduce_rows(acc, red, nr, sum);
-            if (tid < nr * kSB) {
-              const int r = tid / kSB, i = tid % kSB;
-              part_leader[((size_t)(T & 1) * NW + (rank - 1)) * kNRC * kSB + r * kSB + i] = sum[r * kSB + i];
+          }
+        }
+        warp_sum_rows<NW>(acc, nr, sm, w, lane);
+        if (tid < nr * kSB) {
+          const int r = tid / kSB, i = tid % kSB;
+          double s = tree_sum<kSWarps>(&sm.red[0][r][i], kNRC * kSB);
+          if (rank == 1 && T * kSB + i < a.n) s -= __ldcg(bc + T * kSB + i + (long long)r * a.ldb);
+          sm.vec[r][i] = s;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kNRC; ++r) {
+          acc[r] = 0.0;
+          if (r < nr) {
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) acc[r] = fma(sm.lvs[buf][q][tid], sm.vec[r][w + kSWarps * q], acc[r]);
+          }
+        }
+        warp_sum_rows<NW>(acc, nr, sm, w, lane);
+        if (tid < nr * kSB) {
+          const int r = tid / kSB, i = tid % kSB;
+          leader->u.part[T & 1][rank - 1][r][i] = tree_sum<kSWarps>(&sm.red[0][r][i], kNRC * kSB);
+        }
+      };
+
+      // round -1: the workers' shares for the first chain block
+      prefetch(0);
+      if (rank != 0) {
+        worker_step(0);
+        prefetch(1);
+      }
+      cluster.sync();
+      for (int pos = 0; pos < a.S; ++pos) {
+        const int T = fwd ? pos : a.S - 1 - pos;
+        if (rank == 0) {
+          // block T = -(M_T or N_T) * previous block - sum of the workers' shares
+          const int buf = pos & 1;
+          cp_async_wait_all();
+          double acc[kNRC];
+#pragma unroll
+          for (int r = 0; r < kNRC; ++r) {
+            acc[r] = 0.0;
+            if (r < nr) {
+#pragma unroll
+              for (int q = 0; q < kQ; ++q) acc[r] = fma(sm.lvs[buf][q][tid], sm.vec[r][w + kSWarps * q], acc[r]);
             }
           }
+          warp_sum_rows<NW>(acc, nr, sm, w, lane);
+          if (tid < nr * kSB) {
+            const int r = tid / kSB, i = tid % kSB, gi = T * kSB + i;
+            const double y = -(tree_sum<kSWarps>(&sm.red[0][r][i], kNRC * kSB) +
+                               tree_sum<NW>(&sm.u.part[T & 1][0][r][i], kNRC * kSB));
+            sm.vec[r][i] = y;
+            if (gi < a.n) bc[gi + (long long)r * a.ldb] = y;
+            if (a.use_ring) {
+              SolveSmem<NW>* owner = cluster.map_shared_rank(&sm, (T % NW) + 1);
+              owner->u.w.ring[(T / NW) % kRing][r][i] = y;
+            }
+          }
+          prefetch(pos + 1);
+        } else if (pos + 1 < a.S) {
+          worker_step(pos + 1);
+          prefetch(pos + 2);
         }
         cluster.sync();
       }
@@ -200,8 +340,10 @@ __global__ void __launch_bounds__(kSThreads, 1) solve_kernel(SolveArgs a) {
 }
 
 template <int CL>
-static cudaError_t launch_cluster(const SolveArgs& a, cudaStream_t stream, bool* fits) {
-  const size_t smem = sizeof(double) * (size_t)(2 * (CL - 1) * kNRC * kSB + kSWarps * kNRC * kSB + 3 * kNRC * kSB);
+static cudaError_t launch_cluster(const SolveArgs& a0, cudaStream_t stream, bool* fits) {
+  SolveArgs a = a0;
+  a.use_ring = (a.P <= (CL - 1) * (kRing - 1)) ? 1 : 0;
+  const size_t smem = sizeof(SolveSmem<CL - 1>);
   cudaError_t e = cudaFuncSetAttribute(solve_kernel<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (CL > 8) {
@@ -244,11 +386,13 @@ cudaError_t launch_solve(int n, int k, int nrhs, const double* ab, long long lda
   int P = (k + kSB - 1) / kSB;
   if (P > S - 1) P = S - 1;
   double* linv = static_cast<double*>(ws);
-  inv_diag_kernel<<<S, 32, 0, stream>>>(ab, ldab, n, k, linv);
+  double* mfw = linv + (size_t)S * kBlk;
+  double* nbw = mfw + (size_t)S * kBlk;
+  solve_prep_kernel<<<S, 256, 0, stream>>>(ab, ldab, n, k, S, linv, mfw, nbw);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   *launches = 1;
-  SolveArgs a{ab, ldab, n, k, S, P, b, ldb, nrhs, linv};
+  SolveArgs a{ab, ldab, n, k, S, P, b, ldb, nrhs, linv, mfw, nbw, 1};
   bool fits = false;
   e = launch_cluster<16>(a, stream, &fits);
   if (e == cudaSuccess && !fits) e = launch_cluster<8>(a, stream, &fits);
