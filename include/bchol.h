@@ -82,7 +82,8 @@ size_t bchol_workspace_size(bchol_handle_t handle, int n, int k);
  *             the leading minor of order j is not positive definite (LAPACK
  *             pbtrf convention).  When j > 0 the contents of ab are unspecified.
  * The whole factorization is one persistent kernel launch (plus one memset
- * of the ready flags).  Tiles are b x b with b chosen from k (32 or 64).
+ * of the ready flags).  Tiles are b x b with b chosen from k (16 up to
+ * k = 256, else 32) unless bchol_set_tile fixes it.
  */
 bchol_status_t bchol_factor(bchol_handle_t handle, int n, int k, double* ab, int ldab, int* info_dev);
 
@@ -144,12 +145,14 @@ bchol_status_t bchol_set_ctas_per_sm(bchol_handle_t handle, int ctas_per_sm);
 bchol_status_t bchol_set_stall_tile(bchol_handle_t handle, int I, int J);
 
 /* Schedule query (host only, no GPU needed).  The factor kernel walks the
- * tasks of the tiled factorization in ticket order: step s (one outer
- * iteration of Algorithm 1, Sec. 3) is POTRF(s) (type 0), then for each panel
- * row I = s+1..s+m the TRSM(I, s) (type 1) followed by the updates
- * UPD(I, J, s) for J = s+1..I (type 2: A_IJ -= L_Is L_Js^T), with
- * m = min(ceil(k/tile), ceil(n/tile)-1-s).  bchol_plan_task_count returns the
- * number of tasks (or -1 on bad arguments); bchol_plan_task decodes one
+ * tasks of the tiled factorization in ticket order.  Step s (one outer
+ * iteration of Algorithm 1, Sec. 3) has POTRF(s) (type 0), TRSM(I, s) for the
+ * panel rows I = s+1..s+m (type 1) and the updates UPD(I, J, s),
+ * A_IJ -= L_Is L_Js^T, for s < J <= I <= s+m (type 2), with
+ * m = min(ceil(k/tile), ceil(n/tile)-1-s).  Tickets run with one step of
+ * lookahead: panel 0, then per step s the updates of column s+1, the panel of
+ * step s+1, then the other updates of step s.  bchol_plan_task_count returns
+ * the number of tasks (or -1 on bad arguments); bchol_plan_task decodes one
  * ticket into (type, s, I, J) in tile units.  tile is 16, 32 or 64. */
 long long bchol_plan_task_count(int n, int k, int tile);
 bchol_status_t bchol_plan_task(int n, int k, int tile, long long ticket, int* type, int* s, int* I, int* J);

@@ -39,11 +39,13 @@ struct bchol_handle_s {
 
 using namespace bchol;
 
-static int auto_tile(int k) {
-  if (k <= 128) return 16;
-  if (k <= 1024) return 32;
-  return 64;
-}
+// Automatic tile size and CTAs per SM, from the n = 1e5 sweep on GB300:
+// b = 16 wins while the factorization is bound by its step chain (k <= 256);
+// b = 32 wins above.  One CTA per SM keeps the chain's tile operations at the
+// full FP64 rate of an SM (k < 1536); two per SM hide task overheads once
+// the trailing update dominates.
+static int auto_tile(int k) { return k <= 256 ? 16 : 32; }
+static int auto_ctas_per_sm(int k) { return k < 1536 ? 1 : 2; }
 
 static size_t call_bytes(bchol_handle_t h, int n, int k) {
   const int kk = (n > 0 && k > n - 1) ? n - 1 : k;
@@ -189,7 +191,8 @@ bchol_status_t bchol_factor(bchol_handle_t h, int n, int k, double* ab, int ldab
   int* status = reinterpret_cast<int*>(ws);
   h->last_status = status;
   cudaError_t e = launch_factor(P, ab, ldab, info_dev, ws + kStatusBytes, status,
-                                (uint64_t)h->wait_ms * 1000000ull, h->ctas_per_sm, h->stall_I, h->stall_J, h->stream);
+                                (uint64_t)h->wait_ms * 1000000ull, h->ctas_per_sm ? h->ctas_per_sm : auto_ctas_per_sm(kk),
+                                h->stall_I, h->stall_J, h->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return BCHOL_ERR_CUDA;

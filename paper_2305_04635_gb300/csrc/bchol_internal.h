@@ -14,8 +14,8 @@ constexpr int kStatusTimeout = 2;
 // sub-diagonal tiles per panel (clamped to S-1).
 struct FactorPlan {
   int n = 0, k = 0, b = 32, S = 0, p = 0;
-  long long Sreg = 0;          // steps whose panel holds all p sub-diagonal tiles
-  long long Treg = 0;          // tasks per such step: 1 + p(p+3)/2
+  long long Sreg = 0;          // leading ticket blocks of full size (see schedule.cuh)
+  long long Treg = 0;          // tasks per such block: 2p + 1 + p(p-1)/2
   unsigned long long total = 0;  // tasks of the whole factorization
   size_t flag_count = 0;       // ints of ready flags: S*(p+1)
 };

@@ -12,8 +12,9 @@
 //
 // Scheduling replaces the paper's OpenMP task graph (Sec. 3.1) with one
 // persistent launch.  Each CTA claims tasks from a monotone ticket counter in
-// a topological order (step by step; inside a step row by row, so that the
-// tasks that feed step s+1 come first).  Every tile position (I,J) carries a
+// a topological order with one step of lookahead (schedule.cuh): the update
+// of the next panel column and the next panel come before the rest of the
+// current step's trailing update.  Every tile position (I,J) carries a
 // ready counter in global memory, which is the paper's cross-iteration
 // overlap (Sec. 3): the tile of step s+1 that overlaps tile (I+1,J+1) of step
 // s waits for that tile's update, not for a barrier.  The counter of tile
@@ -289,10 +290,12 @@ FactorPlan make_factor_plan(int n, int k, int b) {
   P.S = (n + b - 1) / b;
   P.p = (P.k + b - 1) / b;
   if (P.p > P.S - 1) P.p = P.S - 1;
-  P.Sreg = P.S - P.p;
-  P.Treg = 1 + (long long)P.p * (P.p + 3) / 2;
-  unsigned long long total = (unsigned long long)P.Sreg * (unsigned long long)P.Treg;
-  for (int m = 0; m < P.p; ++m) total += 1 + (unsigned long long)m * (m + 3) / 2;
+  P.Sreg = (P.S - 1 - P.p > 0) ? P.S - 1 - P.p : 0;
+  P.Treg = 2LL * P.p + 1 + (long long)P.p * (P.p - 1) / 2;
+  const Schedule sc{P.S, P.p, P.Sreg, P.Treg};
+  unsigned long long total = 1 + (unsigned long long)sched_m(sc, 0);
+  total += (unsigned long long)P.Sreg * (unsigned long long)P.Treg;
+  for (int s = (int)P.Sreg; s < P.S; ++s) total += (unsigned long long)sched_block_size(sc, s);
   P.total = total;
   P.flag_count = (size_t)P.S * (size_t)(P.p + 1);
   return P;

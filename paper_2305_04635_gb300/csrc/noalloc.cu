@@ -53,8 +53,9 @@ static cudaError_t noalloc_scratch(void** out) {
   return cudaSuccess;
 }
 
-// Tile size for half-bandwidth k; the same rule bchol_factor uses by default.
-static int noalloc_tile(int k) { return k <= 128 ? 16 : (k <= 1024 ? 32 : 64); }
+// Tile size and CTAs per SM for half-bandwidth k; the same rule bchol_factor uses by default.
+static int noalloc_tile(int k) { return k <= 256 ? 16 : 32; }
+static int noalloc_ctas_per_sm(int k) { return k < 1536 ? 1 : 2; }
 
 }  // namespace bchol
 
@@ -75,7 +76,8 @@ extern "C" bchol_status_t bchol_factor_noalloc(void* stream, int n, int k, doubl
     return BCHOL_ERR_CUDA;
   }
   // launch_factor clears the ticket, abort word and ready counters it uses.
-  cudaError_t e = launch_factor(P, ab, ldab, info_dev, scratch, status_dev, 2000ull * 1000000ull, 0, -1, -1, st);
+  cudaError_t e = launch_factor(P, ab, ldab, info_dev, scratch, status_dev, 2000ull * 1000000ull,
+                                noalloc_ctas_per_sm(kk), -1, -1, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return BCHOL_ERR_CUDA;
