@@ -123,6 +123,40 @@ bchol_status_t bchol_factor_noalloc(void* stream, int n, int k, double* ab, int 
 bchol_status_t bchol_solve(bchol_handle_t handle, int n, int k, int nrhs, const double* ab, int ldab,
                            double* b, int ldb);
 
+/*
+ * Batched factorization and solve.  Many independent SPD band systems of
+ * uneven n and k are factored by one persistent launch (the paper factors one
+ * matrix at a time; this is the batched form of the same tile algorithm) and,
+ * for the systems that have right-hand sides, solved by a second launch.
+ * A batch object holds the plan (per-system descriptors, ticket counters and
+ * ready flags, sorted largest system first) in device memory that it
+ * allocates with cudaMalloc when it is planned.
+ *   count            number of systems (>= 1)
+ *   n, k, ldab       HOST arrays of count ints: order, half-bandwidth, leading dimension
+ *   ab               HOST array of count DEVICE pointers: band storage of each A (in place -> L)
+ *   info_dev         DEVICE array of count ints: per-system info (LAPACK convention)
+ *   nrhs, b, ldb     optional (NULL = no solve): HOST arrays; b holds DEVICE pointers to
+ *                    n x nrhs column-major blocks, overwritten by X = A^{-1} B
+ *   tile             16, 32 or 64 (0 = automatic); ctas_per_sm 0 = automatic
+ * bchol_batch_plan synchronises (it copies the descriptors to the device).
+ * bchol_batch_run only enqueues a memset and two kernels on the handle's
+ * stream, so it can be captured in a CUDA graph and replayed; the pointed-to
+ * matrices must then stay at the planned addresses.
+ */
+typedef struct bchol_batch_s* bchol_batch_t;
+bchol_status_t bchol_batch_create(bchol_batch_t* batch);
+bchol_status_t bchol_batch_destroy(bchol_batch_t batch);
+bchol_status_t bchol_batch_plan(bchol_batch_t batch, int count, const int* n, const int* k, double* const* ab,
+                                const int* ldab, int* info_dev, const int* nrhs, double* const* b, const int* ldb,
+                                int tile, int ctas_per_sm);
+bchol_status_t bchol_batch_run(bchol_handle_t handle, bchol_batch_t batch);
+
+/* bchol_factor_batched -- plan + run in one call with the handle's own batch
+ * object and its tile / CTA settings (arguments as for bchol_batch_plan). */
+bchol_status_t bchol_factor_batched(bchol_handle_t handle, int count, const int* n, const int* k, double* const* ab,
+                                    const int* ldab, int* info_dev, const int* nrhs, double* const* b,
+                                    const int* ldb);
+
 /* Wait for the handle's stream, copy `count` device info words to
  * info_host, and return BCHOL_ERR_TIMEOUT if a bounded wait ran out since the
  * last call, else BCHOL_ERR_NOT_SPD if any info > 0, else BCHOL_OK.  Clears

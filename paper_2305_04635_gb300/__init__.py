@@ -74,6 +74,11 @@ def load_library():
         "bchol_set_ctas_per_sm": ([P, I], I),
         "bchol_set_stall_tile": ([P, I, I], I),
         "bchol_last_launch_count": ([P], I),
+        "bchol_batch_create": ([ctypes.POINTER(P)], I),
+        "bchol_batch_destroy": ([P], I),
+        "bchol_batch_plan": ([P, I, P, P, P, P, P, P, P, P, I, I], I),
+        "bchol_batch_run": ([P, P], I),
+        "bchol_factor_batched": ([P, I, P, P, P, P, P, P, P, P], I),
         "bchol_plan_task_count": ([I, I, I], ctypes.c_longlong),
         "bchol_plan_task": ([I, I, I, ctypes.c_longlong, P, P, P, P], I),
         "bchol_version": ([], ctypes.c_char_p),
@@ -261,3 +266,66 @@ def plan_tasks(n: int, k: int, tile: int) -> list[tuple[int, int, int, int]]:
                                                       ctypes.byref(I), ctypes.byref(J)))
         out.append((t.value, s.value, I.value, J.value))
     return out
+
+
+class Batch:
+    """A planned batch of independent band systems (bchol_batch_plan / bchol_batch_run).
+
+    bands: list of band tensors (each (rows, n) with strides (1, ldab)), factored in place.
+    ks:    half-bandwidths.  rhs: optional list of (n,) or (n, nrhs) column-major tensors
+           (None entries = no solve for that system), overwritten by the solutions.
+    The plan keeps the tensors' addresses: run() may be captured in a CUDA graph.
+    """
+
+    def __init__(self, bands, ks, rhs=None, tile: int = 0, ctas_per_sm: int = 0):
+        lib = load_library()
+        self._lib = lib
+        count = len(bands)
+        if count == 0 or len(ks) != count or (rhs is not None and len(rhs) != count):
+            raise ValueError("bands, ks (and rhs) must have the same non-zero length")
+        A = ctypes.c_int * count
+        Pp = ctypes.c_void_p * count
+        ns, lds, ptrs = A(), A(), Pp()
+        kk = A(*[int(k) for k in ks])
+        nr, bp, ldb = A(), Pp(), A()
+        for m, (ab, k) in enumerate(zip(bands, ks)):
+            p, n, ldab = _band_args(ab, int(k))
+            ns[m], lds[m], ptrs[m] = n, ldab, p
+            b = None if rhs is None else rhs[m]
+            if b is None:
+                nr[m], bp[m], ldb[m] = 0, None, max(1, n)
+            else:
+                _require_cuda(b, "rhs")
+                if b.dim() == 1:
+                    nr[m], ldb[m] = 1, max(1, n)
+                else:
+                    nr[m] = b.shape[1]
+                    ldb[m] = b.stride(1) if b.shape[1] > 1 else max(1, n)
+                bp[m] = b.data_ptr()
+        self.info = torch.zeros(count, dtype=torch.int32, device=bands[0].device)
+        self._keep = (list(bands), None if rhs is None else list(rhs), ns, kk, lds, ptrs, nr, bp, ldb)
+        self._b = ctypes.c_void_p()
+        _check("bchol_batch_create", lib.bchol_batch_create(ctypes.byref(self._b)))
+        _check("bchol_batch_plan", lib.bchol_batch_plan(
+            self._b, count, ns, kk, ptrs, lds, ctypes.c_void_p(self.info.data_ptr()),
+            nr if rhs is not None else None, bp if rhs is not None else None, ldb if rhs is not None else None,
+            tile, ctas_per_sm))
+        self.count = count
+
+    def run(self, handle: Handle | None = None) -> torch.Tensor:
+        """Enqueue factor (+ solve) of every system on the handle's stream; returns the device info."""
+        h = _handle(handle)
+        h._sync_stream()
+        _check("bchol_batch_run", self._lib.bchol_batch_run(h.ptr, self._b))
+        return self.info
+
+    def close(self) -> None:
+        if getattr(self, "_b", None) and self._b.value:
+            self._lib.bchol_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

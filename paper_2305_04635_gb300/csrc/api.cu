@@ -35,6 +35,7 @@ struct bchol_handle_s {
   int last_launches = 0;
   int stall_I = -1, stall_J = -1;
   int* last_status = nullptr;  // status word of the workspace used last
+  bchol_batch_t batch = nullptr;  // bchol_factor_batched's own plan
 };
 
 using namespace bchol;
@@ -101,6 +102,7 @@ bchol_status_t bchol_create(bchol_handle_t* handle, void* stream) {
 bchol_status_t bchol_destroy(bchol_handle_t h) {
   if (!h) return BCHOL_ERR_ARG;
   bchol_status_t rc = BCHOL_OK;
+  if (h->batch) bchol_batch_destroy(h->batch);
   if (h->ws_own) {
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = BCHOL_ERR_CUDA;
     cudaFree(h->ws_own);
@@ -219,6 +221,35 @@ bchol_status_t bchol_solve(bchol_handle_t h, int n, int k, int nrhs, const doubl
     return BCHOL_ERR_CUDA;
   }
   return BCHOL_OK;
+}
+
+bchol_status_t bchol_batch_run(bchol_handle_t h, bchol_batch_t batch) {
+  if (!h || !batch) return BCHOL_ERR_ARG;
+  h->last_launches = 0;
+  char* ws = nullptr;
+  bchol_status_t rc = get_workspace(h, kStatusBytes, &ws);
+  if (rc != BCHOL_OK) return rc;
+  int* status = reinterpret_cast<int*>(ws);
+  h->last_status = status;
+  int launches = 0;
+  const int r = batch_run(batch, status, (uint64_t)h->wait_ms * 1000000ull, h->stream, &launches);
+  h->last_launches = launches;
+  if (r != BCHOL_OK) cudaGetLastError();
+  return static_cast<bchol_status_t>(r);
+}
+
+bchol_status_t bchol_factor_batched(bchol_handle_t h, int count, const int* n, const int* k, double* const* ab,
+                                    const int* ldab, int* info_dev, const int* nrhs, double* const* b,
+                                    const int* ldb) {
+  if (!h) return BCHOL_ERR_ARG;
+  if (!h->batch) {
+    bchol_status_t rc = bchol_batch_create(&h->batch);
+    if (rc != BCHOL_OK) return rc;
+  }
+  bchol_status_t rc =
+      bchol_batch_plan(h->batch, count, n, k, ab, ldab, info_dev, nrhs, b, ldb, h->tile, h->ctas_per_sm);
+  if (rc != BCHOL_OK) return rc;
+  return bchol_batch_run(h, h->batch);
 }
 
 bchol_status_t bchol_get_info(bchol_handle_t h, const int* info_dev, int count, int* info_host) {

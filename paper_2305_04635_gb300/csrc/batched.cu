@@ -1,0 +1,466 @@
+// batched.cu -- many independent band systems of uneven n and k in one
+// persistent factor launch plus one solve launch (the batched form of the
+// paper's factorization; the paper itself factors one matrix at a time).
+//
+// Factor: every matrix keeps its own tile schedule (schedule.cuh), ready
+// counters and ticket counter.  A CTA does not block on one matrix: warp 0
+// probes the next ticket of 32 matrices at once, checks whether that task's
+// inputs are already final (acquire loads of its ready counters), and claims
+// the first ready one with a compare-and-swap on that matrix's ticket.  The
+// task then runs with the same code as the single-matrix kernel; its waits
+// return at once.  Since no CTA ever waits for a task that has not started,
+// the launch cannot deadlock; a CTA that finds no ready task for longer than
+// the wait limit records a timeout and stops.  While one matrix's step chain
+// is busy, the CTAs work on the others, which hides the latency of the chain.
+//
+// Solve: one CTA per matrix, largest first, forward then back substitution
+// in blocks of 32 rows (band products of the far blocks spread over the
+// CTA's warps, the 32 x 32 triangular solves on one warp with shuffles).
+#include <algorithm>
+#include <vector>
+
+#include "../../include/bchol.h"
+#include "factor_tasks.cuh"
+
+namespace bchol {
+
+struct BatchMat {
+  double* ab;
+  long long ldab;
+  int n, k, S, p;
+  long long Sreg, Treg;
+  unsigned long long total;
+  long long flag_off;   // offset (ints) of this matrix's ready counters in the pool
+  int* info;
+  double* b;
+  long long ldb;
+  int nrhs;
+  int pad;
+};
+
+struct BatchArgs {
+  const BatchMat* mats;
+  Control* ctl;         // per matrix: ticket, abort word, retired mark
+  int* flags;
+  int count;
+  int* retired;         // number of matrices with no task left to claim
+  unsigned long long* progress;   // tasks claimed so far (all CTAs)
+  int* status;
+  uint64_t wait_ns;
+};
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ FactorArgs matrix_args(const BatchArgs& g, int m) {
+  const BatchMat& M = g.mats[m];
+  FactorArgs a;
+  a.ab = M.ab;
+  a.ldab = M.ldab;
+  a.n = M.n;
+  a.k = M.k;
+  a.S = M.S;
+  a.p = M.p;
+  a.Sreg = M.Sreg;
+  a.Treg = M.Treg;
+  a.total = M.total;
+  a.flags = g.flags + M.flag_off;
+  a.ctl = g.ctl + m;
+  a.status = g.status;
+  a.info = M.info;
+  a.wait_ns = g.wait_ns;
+  a.stall = -1;
+  return a;
+}
+
+// Are the inputs of task (type, s, I, J) final?  The same targets as the waits in the tasks.
+__device__ __forceinline__ bool task_ready(const FactorArgs& a, int type, int s, int I, int J) {
+  if (type == kPotrf) return ld_acquire(&a.flags[fidx(a, s, s)]) >= s - first_step(a, s);
+  if (type == kTrsm)
+    return ld_acquire(&a.flags[fidx(a, s, s)]) >= s - first_step(a, s) + 1 &&
+           ld_acquire(&a.flags[fidx(a, I, s)]) >= s - first_step(a, I);
+  return ld_acquire(&a.flags[fidx(a, I, s)]) >= s - first_step(a, I) + 1 &&
+         ld_acquire(&a.flags[fidx(a, J, s)]) >= s - first_step(a, J) + 1 &&
+         ld_acquire(&a.flags[fidx(a, I, J)]) >= s - first_step(a, I);
+}
+
+template <int B>
+__global__ void __launch_bounds__(kThreads, 2) factor_batched_kernel(BatchArgs g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem<B>& sm = *reinterpret_cast<Smem<B>*>(smem_raw);
+  __shared__ int s_m, s_go, s_flag;
+  __shared__ long long s_t;
+  const int tid = threadIdx.x, lane = tid & 31;
+  int m0 = blockIdx.x % g.count;   // where this CTA's search starts
+  uint64_t idle_since = 0;
+  unsigned long long seen = 0;
+  if (tid == 0) idle_since = globaltimer_ns();
+  while (true) {
+    if (tid < 32) {
+      int go = 0, mm_won = -1;
+      long long t_won = 0;
+      const int rounds = (g.count + 31) / 32;
+      for (int rd = 0; rd < rounds && !go; ++rd) {
+        const int mm = (m0 + rd * 32 + lane) % g.count;
+        bool ready = false;
+        unsigned long long t = 0;
+        if (rd * 32 + lane < g.count) {
+          Control* c = g.ctl + mm;
+          if (ld_relaxed(&c->pad) == 0) {
+            t = ld_relaxed_u64(&c->ticket);
+            const FactorArgs a = matrix_args(g, mm);
+            if (t >= a.total || ld_relaxed(&c->abort) != 0) {
+              if (atomicCAS(&c->pad, 0, 1) == 0) atomicAdd(g.retired, 1);
+            } else {
+              int type, s, I, J;
+              decode_task(Schedule{a.S, a.p, a.Sreg, a.Treg}, (long long)t, type, s, I, J);
+              ready = task_ready(a, type, s, I, J);
+            }
+          }
+        }
+        unsigned ballot = __ballot_sync(0xffffffffu, ready);
+        while (ballot && !go) {
+          const int f = __ffs(ballot) - 1;
+          int won = 0;
+          if (lane == f) won = (atomicCAS(&g.ctl[mm].ticket, t, t + 1) == t);
+          won = __shfl_sync(0xffffffffu, won, f);
+          if (won) {
+            go = 1;
+            mm_won = __shfl_sync(0xffffffffu, mm, f);
+            t_won = (long long)__shfl_sync(0xffffffffu, (unsigned long long)t, f);
+          }
+          ballot &= ballot - 1;
+        }
+      }
+      if (lane == 0) {
+        if (go) {
+          s_go = 1;
+          s_m = mm_won;
+          s_t = t_won;
+          m0 = mm_won;   // prefer the same matrix next time: its next ticket is often ready
+          atomicAdd(g.progress, 1ULL);
+          idle_since = globaltimer_ns();
+        } else if (ld_relaxed(g.retired) >= g.count) {
+          s_go = -1;
+        } else {
+          s_go = 0;
+          m0 = (m0 + 32) % g.count;
+          // a stall only if no CTA has claimed a task for the whole wait limit
+          const unsigned long long now_seen = ld_relaxed_u64(g.progress);
+          const uint64_t now = globaltimer_ns();
+          if (now_seen != seen) {
+            seen = now_seen;
+            idle_since = now;
+          } else if (now - idle_since > g.wait_ns) {
+            atomicExch(g.status, kStatusTimeout);
+            s_go = -1;
+          }
+        }
+      }
+      m0 = __shfl_sync(0xffffffffu, m0, 0);
+    }
+    __syncthreads();
+    const int go = s_go;
+    if (go < 0) break;
+    if (go == 0) {
+      if (tid == 0) __nanosleep(200);
+      __syncthreads();
+      continue;
+    }
+    const FactorArgs a = matrix_args(g, s_m);
+    int type, s, I, J;
+    decode_task(Schedule{a.S, a.p, a.Sreg, a.Treg}, s_t, type, s, I, J);
+    if (type == kPotrf)
+      task_potrf<B>(a, s, sm, &s_flag);
+    else if (type == kTrsm)
+      task_trsm<B>(a, I, s, sm, &s_flag);
+    else
+      task_upd<B>(a, I, J, s, sm, &s_flag);
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ solve
+constexpr int kBS = 32;     // rows per block
+constexpr int kBR = 8;      // right-hand sides per pass
+
+__device__ __forceinline__ double lb(const BatchMat& M, int gi, int gj) {
+  const int d = gi - gj;
+  return (gi < M.n && gj >= 0 && d >= 0 && d <= M.k) ? __ldg(M.ab + d + (long long)gj * M.ldab) : 0.0;
+}
+
+// One warp: solve the 32 x 32 lower (fwd) or upper (L^T, bwd) triangle of diagonal block I
+// for v[r] (lane = row), r < nr.  Rows past n stay zero.
+template <bool fwd>
+__device__ __forceinline__ void tri_solve_warp(const BatchMat& M, int I, double (&v)[kBR], int nr, int lane) {
+  const int gi = I * kBS + lane;
+  const bool live = gi < M.n;
+  double col[kBS];   // fwd: L(i, j) for j (row i of the tile); bwd: L(j, i) for j (column i)
+#pragma unroll
+  for (int j = 0; j < kBS; ++j) col[j] = fwd ? lb(M, gi, I * kBS + j) : lb(M, I * kBS + j, gi);
+  const double rinv = live ? 1.0 / lb(M, gi, gi) : 0.0;
+#pragma unroll
+  for (int jj = 0; jj < kBS; ++jj) {
+    const int j = fwd ? jj : kBS - 1 - jj;
+#pragma unroll
+    for (int r = 0; r < kBR; ++r) {
+      if (r < nr) {
+        double x = (lane == j) ? v[r] * rinv : 0.0;
+        x = __shfl_sync(0xffffffffu, x, j);
+        if (lane == j) v[r] = x;
+        else if (fwd ? (lane > j) : (lane < j)) v[r] = fma(-col[j], x, v[r]);
+      }
+    }
+  }
+  if (!live) {
+#pragma unroll
+    for (int r = 0; r < kBR; ++r) v[r] = 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(256) solve_batched_kernel(const BatchMat* mats, const int* order, int count,
+                                                            unsigned* queue) {
+  __shared__ double red[8][kBR][kBS];
+  __shared__ int s_m;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  while (true) {
+    if (tid == 0) {
+      const unsigned q = atomicAdd(queue, 1u);
+      s_m = (q < (unsigned)count) ? order[q] : -1;
+    }
+    __syncthreads();
+    const int m = s_m;
+    __syncthreads();
+    if (m < 0) break;
+    const BatchMat& M = mats[m];
+    if (M.nrhs <= 0 || M.n <= 0 || __ldcg(M.info) != 0) continue;
+    const int S = (M.n + kBS - 1) / kBS;
+    int P = (M.k + kBS - 1) / kBS;
+    if (P > S - 1) P = S - 1;
+    for (int c0 = 0; c0 < M.nrhs; c0 += kBR) {
+      const int nr = min(kBR, M.nrhs - c0);
+      double* bc = M.b + (long long)c0 * M.ldb;
+      for (int sweep = 0; sweep < 2; ++sweep) {
+        const bool fwd = (sweep == 0);
+        for (int step = 0; step < S; ++step) {
+          const int I = fwd ? step : S - 1 - step;
+          // far blocks: lane = row i of block I, warp w takes columns c = w, w+8, ...
+          double acc[kBR];
+#pragma unroll
+          for (int r = 0; r < kBR; ++r) acc[r] = 0.0;
+          const int jlo = fwd ? max(0, I - P) : I + 1;
+          const int jhi = fwd ? I - 1 : min(S - 1, I + P);
+          const int gi = I * kBS + lane;
+          for (int J = jlo; J <= jhi; ++J) {
+#pragma unroll
+            for (int q = 0; q < kBS / 8; ++q) {
+              const int gc = J * kBS + w + 8 * q;
+              if (gc < M.n) {
+                const double mv = fwd ? lb(M, gi, gc) : lb(M, gc, gi);
+#pragma unroll
+                for (int r = 0; r < kBR; ++r)
+                  if (r < nr) acc[r] = fma(mv, __ldcg(bc + gc + (long long)r * M.ldb), acc[r]);
+              }
+            }
+          }
+#pragma unroll
+          for (int r = 0; r < kBR; ++r)
+            if (r < nr) red[w][r][lane] = acc[r];
+          __syncthreads();
+          if (w == 0) {
+            double v[kBR];
+#pragma unroll
+            for (int r = 0; r < kBR; ++r) {
+              v[r] = 0.0;
+              if (r < nr) {
+                double s = 0.0;
+#pragma unroll
+                for (int ww = 0; ww < 8; ++ww) s += red[ww][r][lane];
+                v[r] = (gi < M.n ? __ldcg(bc + gi + (long long)r * M.ldb) : 0.0) - s;
+              }
+            }
+            if (fwd)
+              tri_solve_warp<true>(M, I, v, nr, lane);
+            else
+              tri_solve_warp<false>(M, I, v, nr, lane);
+#pragma unroll
+            for (int r = 0; r < kBR; ++r)
+              if (r < nr && gi < M.n) bc[gi + (long long)r * M.ldb] = v[r];
+          }
+          __syncthreads();
+        }
+      }
+    }
+  }
+}
+
+}  // namespace bchol
+
+// ------------------------------------------------------------------ host side
+using namespace bchol;
+
+struct bchol_batch_s {
+  int count = 0;
+  int b = 32;
+  int ctas_per_sm = 1;
+  bool any_rhs = false;
+  int* info_dev = nullptr;
+  size_t bytes = 0;
+  void* dev = nullptr;          // descriptors | order | control | flags | counters
+  size_t ctl_off = 0, flags_off = 0, cnt_off = 0, order_off = 0, clear_bytes = 0;
+};
+
+extern "C" bchol_status_t bchol_batch_create(bchol_batch_t* batch) {
+  if (!batch) return BCHOL_ERR_ARG;
+  *batch = new (std::nothrow) bchol_batch_s();
+  return *batch ? BCHOL_OK : BCHOL_ERR_ALLOC;
+}
+
+extern "C" bchol_status_t bchol_batch_destroy(bchol_batch_t batch) {
+  if (!batch) return BCHOL_ERR_ARG;
+  if (batch->dev) cudaFree(batch->dev);
+  delete batch;
+  return BCHOL_OK;
+}
+
+extern "C" bchol_status_t bchol_batch_plan(bchol_batch_t batch, int count, const int* n, const int* k, double* const* ab,
+                                           const int* ldab, int* info_dev, const int* nrhs, double* const* b,
+                                           const int* ldb, int tile, int ctas_per_sm) {
+  if (!batch || count <= 0 || !n || !k || !ab || !ldab || !info_dev) return BCHOL_ERR_ARG;
+  if (!(tile == 0 || tile == 16 || tile == 32 || tile == 64) || ctas_per_sm < 0 || ctas_per_sm > 8) return BCHOL_ERR_ARG;
+  int kmax = 0;
+  for (int m = 0; m < count; ++m) {
+    if (n[m] < 1 || k[m] < 0 || ldab[m] < k[m] + 1 || !ab[m]) return BCHOL_ERR_ARG;
+    const int r = nrhs ? nrhs[m] : 0;
+    if (r < 0 || (r > 0 && (!b || !b[m] || !ldb || ldb[m] < n[m]))) return BCHOL_ERR_ARG;
+    kmax = std::max(kmax, std::min(k[m], n[m] - 1));
+  }
+  const int bt = tile ? tile : (kmax <= 256 ? 16 : 32);
+  std::vector<BatchMat> mats(count);
+  std::vector<double> work(count);
+  size_t flag_total = 0;
+  bool any_rhs = false;
+  for (int m = 0; m < count; ++m) {
+    const int kk = std::min(k[m], n[m] - 1);
+    const FactorPlan P = make_factor_plan(n[m], kk, bt);
+    BatchMat& M = mats[m];
+    M.ab = ab[m];
+    M.ldab = ldab[m];
+    M.n = n[m];
+    M.k = kk;
+    M.S = P.S;
+    M.p = P.p;
+    M.Sreg = P.Sreg;
+    M.Treg = P.Treg;
+    M.total = P.total;
+    M.flag_off = (long long)flag_total;
+    M.info = info_dev + m;
+    M.nrhs = nrhs ? nrhs[m] : 0;
+    M.b = M.nrhs ? b[m] : nullptr;
+    M.ldb = M.nrhs ? ldb[m] : 1;
+    M.pad = 0;
+    flag_total += P.flag_count;
+    any_rhs = any_rhs || M.nrhs > 0;
+    work[m] = (double)n[m] * (kk + 1.0) * (kk + 4.0);
+  }
+  // largest matrices first: both kernels take them in this order
+  std::vector<int> order(count);
+  for (int m = 0; m < count; ++m) order[m] = m;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
+  std::vector<BatchMat> sorted(count);
+  for (int q = 0; q < count; ++q) sorted[q] = mats[order[q]];
+  std::vector<int> solve_order(count);
+  for (int q = 0; q < count; ++q) solve_order[q] = q;   // indices into the sorted descriptors
+  auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t desc_b = up(sizeof(BatchMat) * count);
+  const size_t order_b = up(sizeof(int) * count);
+  const size_t ctl_b = up(sizeof(Control) * count);
+  const size_t flags_b = up(sizeof(int) * flag_total);
+  const size_t cnt_b = 256;
+  const size_t need = desc_b + order_b + ctl_b + flags_b + cnt_b;
+  if (batch->bytes < need) {
+    if (batch->dev) {
+      cudaDeviceSynchronize();
+      cudaFree(batch->dev);
+      batch->dev = nullptr;
+      batch->bytes = 0;
+    }
+    if (cudaMalloc(&batch->dev, need) != cudaSuccess) {
+      cudaGetLastError();
+      return BCHOL_ERR_ALLOC;
+    }
+    batch->bytes = need;
+  }
+  char* base = static_cast<char*>(batch->dev);
+  batch->order_off = desc_b;
+  batch->ctl_off = desc_b + order_b;
+  batch->flags_off = batch->ctl_off + ctl_b;
+  batch->cnt_off = batch->flags_off + flags_b;
+  batch->clear_bytes = ctl_b + flags_b + cnt_b;   // control, flags and counters are contiguous
+  if (cudaMemcpy(base, sorted.data(), sizeof(BatchMat) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(base + batch->order_off, solve_order.data(), sizeof(int) * count, cudaMemcpyHostToDevice) !=
+          cudaSuccess)
+    return BCHOL_ERR_CUDA;
+  batch->count = count;
+  batch->b = bt;
+  batch->ctas_per_sm = ctas_per_sm ? ctas_per_sm : (kmax < 1536 ? 1 : 2);
+  batch->any_rhs = any_rhs;
+  batch->info_dev = info_dev;
+  return BCHOL_OK;
+}
+
+template <int B>
+static cudaError_t launch_batched_factor(const BatchArgs& g, int ctas_per_sm, cudaStream_t st) {
+  const size_t smem = sizeof(Smem<B>);
+  cudaError_t e = cudaFuncSetAttribute(factor_batched_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, factor_batched_kernel<B>, kThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+  factor_batched_kernel<B><<<per_sm * num_sms(), kThreads, smem, st>>>(g);
+  return cudaGetLastError();
+}
+
+// Launches for a planned batch (capturable in a CUDA graph): clear the
+// control words, factor every matrix, then solve those with right-hand sides.
+namespace bchol {
+int batch_run(bchol_batch_s* batch, int* status, uint64_t wait_ns, cudaStream_t st, int* launches) {
+  *launches = 0;
+  if (!batch || batch->count <= 0 || !batch->dev) return BCHOL_ERR_ARG;
+  char* base = static_cast<char*>(batch->dev);
+  if (cudaMemsetAsync(base + batch->ctl_off, 0, batch->clear_bytes, st) != cudaSuccess ||
+      cudaMemsetAsync(batch->info_dev, 0, sizeof(int) * batch->count, st) != cudaSuccess)
+    return BCHOL_ERR_CUDA;
+  BatchArgs g;
+  g.mats = reinterpret_cast<const BatchMat*>(base);
+  g.ctl = reinterpret_cast<Control*>(base + batch->ctl_off);
+  g.flags = reinterpret_cast<int*>(base + batch->flags_off);
+  g.count = batch->count;
+  g.retired = reinterpret_cast<int*>(base + batch->cnt_off);
+  g.progress = reinterpret_cast<unsigned long long*>(base + batch->cnt_off + 128);
+  g.status = status;
+  g.wait_ns = wait_ns;
+  cudaError_t e;
+  switch (batch->b) {
+    case 16: e = launch_batched_factor<16>(g, batch->ctas_per_sm, st); break;
+    case 32: e = launch_batched_factor<32>(g, batch->ctas_per_sm, st); break;
+    default: e = launch_batched_factor<64>(g, batch->ctas_per_sm, st); break;
+  }
+  if (e != cudaSuccess) return BCHOL_ERR_CUDA;
+  *launches = 1;
+  if (batch->any_rhs) {
+    unsigned* queue = reinterpret_cast<unsigned*>(base + batch->cnt_off + 64);
+    const int grid = std::min(batch->count, 4 * num_sms());
+    solve_batched_kernel<<<grid, 256, 0, st>>>(g.mats, reinterpret_cast<const int*>(base + batch->order_off),
+                                               batch->count, queue);
+    if (cudaGetLastError() != cudaSuccess) return BCHOL_ERR_CUDA;
+    *launches = 2;
+  }
+  return BCHOL_OK;
+}
+}  // namespace bchol

@@ -39,3 +39,10 @@ cudaError_t launch_solve(int n, int k, int nrhs, const double* ab, long long lda
 int num_sms();
 
 }  // namespace bchol
+
+struct bchol_batch_s;
+namespace bchol {
+// Enqueue the launches of a planned batch (batched.cu).
+int batch_run(bchol_batch_s* batch, int* status, uint64_t wait_ns, cudaStream_t stream, int* launches);
+
+}  // namespace bchol

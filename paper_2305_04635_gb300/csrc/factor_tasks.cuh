@@ -1,0 +1,236 @@
+// factor_tasks.cuh -- the tile tasks of the band factorization (POTRF, TRSM,
+// UPD), shared by the single-matrix and the batched persistent kernels.
+// The method and the ready-counter protocol are described in factor.cu.
+#pragma once
+#include "bchol_device.cuh"
+#include "bchol_internal.h"
+#include "schedule.cuh"
+
+namespace bchol {
+
+struct FactorArgs {
+  double* ab;
+  long long ldab;
+  int n, k, S, p;
+  long long Sreg, Treg;
+  unsigned long long total;
+  int* flags;
+  Control* ctl;
+  int* status;
+  int* info;
+  uint64_t wait_ns;
+  int stall;  // flag index whose waits never succeed (failure-path test hook), or -1
+};
+
+__device__ __forceinline__ int fidx(const FactorArgs& a, int I, int J) { return J * (a.p + 1) + (I - J); }
+__device__ __forceinline__ int first_step(const FactorArgs& a, int I) { return I - a.p > 0 ? I - a.p : 0; }
+
+// Wait (one thread) until the ready counter of tile (I,J) reaches `target`.
+__device__ __forceinline__ bool wait_tile(const FactorArgs& a, int I, int J, int target) {
+  const int f = fidx(a, I, J);
+  if (f == a.stall) target = 0x7fffffff;
+  return wait_flag_geq(&a.flags[f], target, a.ctl, a.status, a.wait_ns);
+}
+
+constexpr int kThreads = 256;
+
+template <int B>
+struct Smem {
+  double t0[B * B];
+  double t1[B * B];
+};
+
+// Publish: every thread's stores are done (barrier), then one release store.
+__device__ __forceinline__ void publish(int* flag, int value) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    st_release(flag, value);
+  }
+}
+
+// ---------------------------------------------------------------- POTRF(s)
+// Right-looking Cholesky of the diagonal tile in shared memory, one column
+// per barrier.  TPR threads share a row; the thread that updates the next
+// pivot computes its reciprocal square root right away, so the pivot is ready
+// when the barrier opens.  A pivot that is not > 0 (NaN included) stops the
+// launch and sets info to its 1-based global column (LAPACK convention).
+template <int B>
+__device__ bool task_potrf(const FactorArgs& a, int s, Smem<B>& sm, int* s_flag) {
+  constexpr int TPR = kThreads / B;
+  __shared__ double s_rinv[B], s_ljj[B];
+  __shared__ int s_fail;
+  const int tid = threadIdx.x;
+  const int s0 = first_step(a, s);
+  if (tid == 0) *s_flag = wait_tile(a, s, s, s - s0);
+  __syncthreads();
+  if (!*s_flag) return false;
+  double* sA = sm.t0;
+  double* sL = sm.t1;
+  load_tile<B, kThreads>(a.ab, a.ldab, a.n, a.k, s, s, sA);
+  for (int idx = tid; idx < B * B; idx += kThreads) sL[idx] = 0.0;
+  const int jmax = min(B, a.n - s * B);
+  __syncthreads();
+  if (tid == 0) {
+    s_fail = 0;
+    const double d = sA[0];
+    if (!(d > 0.0)) {
+      s_fail = 1;
+    } else {
+      const double r = rsqrt(d);
+      s_rinv[0] = r;
+      s_ljj[0] = d * r;
+    }
+  }
+  __syncthreads();
+  const int i = tid / TPR, sub = tid % TPR;
+  for (int j = 0; j < jmax; ++j) {
+    if (s_fail) break;
+    const double r = s_rinv[j];
+    if (i > j && i < jmax) {
+      const double x = sA[j * B + i] * r;  // L(i,j)
+      const double y = x * r;              // A(i,j) / A(j,j)
+      if (sub == 0) sL[j * B + i] = x;
+      for (int l = j + 1 + sub; l <= i; l += TPR) {
+        const double v = fma(-y, sA[j * B + l], sA[l * B + i]);
+        sA[l * B + i] = v;
+        if (l == i && i == j + 1) {  // the next pivot
+          if (!(v > 0.0)) {
+            s_fail = j + 2;
+          } else {
+            const double rr = rsqrt(v);
+            s_rinv[j + 1] = rr;
+            s_ljj[j + 1] = v * rr;
+          }
+        }
+      }
+    }
+    if (tid == 0) sL[j * B + j] = s_ljj[j];
+    __syncthreads();
+  }
+  if (s_fail) {
+    if (tid == 0) {
+      atomicCAS(a.info, 0, s * B + s_fail);
+      atomicExch(&a.ctl->abort, 1);
+    }
+    return false;
+  }
+  store_tile<B, kThreads>(a.ab, a.ldab, a.n, a.k, s, s, sL);
+  publish(&a.flags[fidx(a, s, s)], s - s0 + 1);
+  return true;
+}
+
+// ---------------------------------------------------------------- TRSM(I,s)
+// X = A_Is L_ss^{-T}, row by row: TPR threads own a row, thread `sub` keeps
+// the columns l = sub (mod TPR) in registers; column j's value is formed by
+// its owner and shuffled to the row group.  No block barriers in the loop.
+template <int B>
+__device__ bool task_trsm(const FactorArgs& a, int I, int s, Smem<B>& sm, int* s_flag) {
+  constexpr int TPR = kThreads / B;
+  constexpr int R = B / TPR;
+  __shared__ double s_rinv[B];
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    bool ok = wait_tile(a, s, s, s - first_step(a, s) + 1);
+    if (ok) ok = wait_tile(a, I, s, s - first_step(a, I));
+    *s_flag = ok;
+  }
+  __syncthreads();
+  if (!*s_flag) return false;
+  double* sX = sm.t0;
+  double* sL = sm.t1;
+  load_tile<B, kThreads>(a.ab, a.ldab, a.n, a.k, I, s, sX);
+  load_tile<B, kThreads>(a.ab, a.ldab, a.n, a.k, s, s, sL);
+  __syncthreads();
+  const int jmax = min(B, a.n - s * B);
+  if (tid < B) s_rinv[tid] = (tid < jmax) ? 1.0 / sL[tid * B + tid] : 0.0;
+  const int i = tid / TPR, sub = tid % TPR;
+  double acc[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) acc[q] = sX[(sub + q * TPR) * B + i];
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < B; ++j) {
+    const int owner = j % TPR, qj = j / TPR;
+    double x = 0.0;
+    if (sub == owner) {
+      x = acc[qj] * s_rinv[j];
+      acc[qj] = x;
+    }
+    x = __shfl_sync(0xffffffffu, x, owner, TPR);
+#pragma unroll
+    for (int q = qj; q < R; ++q) {
+      const int l = sub + q * TPR;
+      if (l > j) acc[q] = fma(-x, sL[j * B + l], acc[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < R; ++q) sX[(sub + q * TPR) * B + i] = acc[q];
+  __syncthreads();
+  store_tile<B, kThreads>(a.ab, a.ldab, a.n, a.k, I, s, sX);
+  publish(&a.flags[fidx(a, I, s)], s - first_step(a, I) + 1);
+  return true;
+}
+
+// ---------------------------------------------------------------- UPD(I,J,s)
+// A_IJ -= L_Is L_Js^T: the two panel tiles are staged in shared memory, the
+// updated tile stays in registers (an R x R block per thread, rows ty+16r and
+// columns tx+16c).  On a diagonal tile (the DSYRK case) the blocks that lie
+// wholly above the diagonal are skipped.
+template <int B>
+__device__ bool task_upd(const FactorArgs& a, int I, int J, int s, Smem<B>& sm, int* s_flag) {
+  constexpr int R = B / 16;
+  const int tid = threadIdx.x;
+  const int s0I = first_step(a, I);
+  if (tid == 0) {
+    bool ok = wait_tile(a, I, s, s - s0I + 1);
+    if (ok && J != I) ok = wait_tile(a, J, s, s - first_step(a, J) + 1);
+    if (ok) ok = wait_tile(a, I, J, s - s0I);
+    *s_flag = ok;
+  }
+  __syncthreads();
+  if (!*s_flag) return false;
+  double* sA = sm.t0;
+  double* sB = sm.t1;
+  load_tile<B, kThreads>(a.ab, a.ldab, a.n, a.k, I, s, sA);
+  if (J != I) load_tile<B, kThreads>(a.ab, a.ldab, a.n, a.k, J, s, sB);
+  const double* sBr = (J != I) ? sB : sA;
+  const int ty = tid / 16, tx = tid % 16;
+  const bool diag = (I == J);
+  double acc[R][R];
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int c = 0; c < R; ++c) {
+      const int gi = I * B + ty + 16 * r, gj = J * B + tx + 16 * c;
+      const int d = gi - gj;
+      acc[r][c] = (gi < a.n && d >= 0 && d <= a.k) ? __ldcg(a.ab + d + (long long)gj * a.ldab) : 0.0;
+    }
+  __syncthreads();
+#pragma unroll 4
+  for (int l = 0; l < B; ++l) {
+    double av[R], bv[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) av[r] = sA[l * B + ty + 16 * r];
+#pragma unroll
+    for (int c = 0; c < R; ++c) bv[c] = sBr[l * B + tx + 16 * c];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int c = 0; c < R; ++c)
+        if (!(diag && r < c)) acc[r][c] = fma(-av[r], bv[c], acc[r][c]);
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int c = 0; c < R; ++c) {
+      const int gi = I * B + ty + 16 * r, gj = J * B + tx + 16 * c;
+      const int d = gi - gj;
+      if (gi < a.n && d >= 0 && d <= a.k) a.ab[d + (long long)gj * a.ldab] = acc[r][c];
+    }
+  publish(&a.flags[fidx(a, I, J)], s - s0I + 1);
+  return true;
+}
+
+
+}  // namespace bchol
