@@ -124,6 +124,59 @@ bchol_status_t bchol_solve(bchol_handle_t handle, int n, int k, int nrhs, const 
                            double* b, int ldb);
 
 /*
+ * bchol_logdet -- log det A = 2 sum_i log L_ii from the factor in ab, written
+ * to the device double out_dev (asynchronous).
+ */
+bchol_status_t bchol_logdet(bchol_handle_t handle, int n, const double* ab, int ldab, double* out_dev);
+
+/*
+ * bchol_backward -- the adjoint of x = A^{-1} b and log det A with respect to
+ * the stored band of A (the interior-point use the paper names, Sec. 1-2).
+ * For a scalar loss f(x, log det A) with xbar = df/dx and ldbar = df/dlogdet:
+ *   bbar = A^{-1} xbar   (df/db)
+ *   abar(i,j) = 2 ldbar Sigma(i,j) - (bbar_i x_j + bbar_j x_i)   for i > j
+ *   abar(i,i) =   ldbar Sigma(i,i) -  bbar_i x_i
+ * where Sigma = A^{-1}; each stored off-diagonal entry ab(i-j, j) stands for
+ * both A(i,j) and A(j,i), hence the factor 2 and the symmetric term.  Only the
+ * band of Sigma is formed, by selected inversion (the Takahashi recurrences
+ * Sigma L = L^{-T}) in one persistent kernel over the factor's tiles, walked
+ * from the last block column to the first.
+ *   ab, ldab      device, the factor L from bchol_factor (read only)
+ *   x             device, the solution x = A^{-1} b (n doubles; may be NULL if xbar is NULL)
+ *   xbar          device, df/dx (n doubles), or NULL for a loss of log det A alone
+ *   ldbar         df/dlogdet
+ *   abar, ldabar  device, output band (ldabar >= k+1): df/d ab
+ *   bbar          device, output df/db (n doubles; may be NULL if xbar is NULL)
+ */
+bchol_status_t bchol_backward(bchol_handle_t handle, int n, int k, const double* ab, int ldab, const double* x,
+                              const double* xbar, double ldbar, double* abar, int ldabar, double* bbar);
+
+/*
+ * bchol_solve_mixed -- X = A^{-1} B by a mixed-precision factorization with
+ * FP64 iterative refinement.  The paper's method is FP64 throughout; this
+ * form runs the trailing SYRK/GEMM updates of Algorithm 1 (the O(n k^2) part,
+ * Sec. 3.2) with FP32 accumulation, keeps POTRF and TRSM of the tiles in FP64,
+ * and recovers FP64 accuracy by refinement:
+ *   Ã = S A S, S = diag(A)^{-1/2} (equilibration of a copy of A; A is not changed)
+ *   Ã ~ L L^T (FP32-accumulated updates); x_0 = S (L L^T)^{-1} S b
+ *   repeat: r = b - A x (FP64); stop when max_c ||r_c|| / ||b_c|| <= tol, when the
+ *   residual stops shrinking or after max_iter corrections; else d = S (L L^T)^{-1} S r
+ *   (FP32 solve) and x += d (FP64).
+ *   ab, ldab      device, lower band of A (read only)
+ *   b, ldb        device, n x nrhs right-hand sides (read only)
+ *   x, ldx        device, n x nrhs solution (output)
+ *   info_dev      device int: info of the factorization of Ã (LAPACK convention)
+ *   iters, resid, corr   host outputs: corrections made, final max_c ||b_c - A x_c|| / ||b_c||,
+ *                 and the last relative correction max_c ||d_c|| / ||x_c|| (0 if none)
+ * Returns BCHOL_ERR_NOT_SPD (with info_dev set) if Ã is not positive definite.
+ * Synchronises the handle's stream (the loop reads the norms on the host).
+ * Workspace: a copy of the band, n x nrhs doubles and the factor/solve scratch.
+ */
+bchol_status_t bchol_solve_mixed(bchol_handle_t handle, int n, int k, int nrhs, const double* ab, int ldab,
+                                 const double* b, int ldb, double* x, int ldx, int max_iter, double tol,
+                                 int* info_dev, int* iters, double* resid, double* corr);
+
+/*
  * Batched factorization and solve.  Many independent SPD band systems of
  * uneven n and k are factored by one persistent launch (the paper factors one
  * matrix at a time; this is the batched form of the same tile algorithm) and,

@@ -74,6 +74,9 @@ def load_library():
         "bchol_set_ctas_per_sm": ([P, I], I),
         "bchol_set_stall_tile": ([P, I, I], I),
         "bchol_last_launch_count": ([P], I),
+        "bchol_solve_mixed": ([P, I, I, I, P, I, P, I, P, I, I, ctypes.c_double, P, P, P, P], I),
+        "bchol_logdet": ([P, I, P, I, P], I),
+        "bchol_backward": ([P, I, I, P, I, P, P, ctypes.c_double, P, I, P], I),
         "bchol_batch_create": ([ctypes.POINTER(P)], I),
         "bchol_batch_destroy": ([P], I),
         "bchol_batch_plan": ([P, I, P, P, P, P, P, P, P, P, I, I], I),

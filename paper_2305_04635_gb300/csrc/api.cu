@@ -223,6 +223,80 @@ bchol_status_t bchol_solve(bchol_handle_t h, int n, int k, int nrhs, const doubl
   return BCHOL_OK;
 }
 
+bchol_status_t bchol_logdet(bchol_handle_t h, int n, const double* ab, int ldab, double* out_dev) {
+  if (!h || n < 1 || ldab < 1 || !ab || !out_dev) return BCHOL_ERR_ARG;
+  h->last_launches = 0;
+  if (launch_logdet(ab, ldab, n, out_dev, h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return BCHOL_ERR_CUDA;
+  }
+  h->last_launches = 1;
+  return BCHOL_OK;
+}
+
+bchol_status_t bchol_backward(bchol_handle_t h, int n, int k, const double* ab, int ldab, const double* x,
+                              const double* xbar, double ldbar, double* abar, int ldabar, double* bbar) {
+  if (!h || n < 1 || k < 0 || ldab < k + 1 || ldabar < k + 1 || !ab || !abar) return BCHOL_ERR_ARG;
+  if ((xbar != nullptr) && (!x || !bbar)) return BCHOL_ERR_ARG;
+  h->last_launches = 0;
+  const int kk = k > n - 1 ? n - 1 : k;
+  const int b = h->tile ? h->tile : auto_tile(kk);
+  size_t need = call_bytes(h, n, k);
+  const size_t sel = kStatusBytes + selinv_workspace_bytes(n, kk, b);
+  if (sel > need) need = sel;
+  char* ws = nullptr;
+  bchol_status_t rc = get_workspace(h, need, &ws);
+  if (rc != BCHOL_OK) return rc;
+  int* status = reinterpret_cast<int*>(ws);
+  h->last_status = status;
+  int launches = 0;
+  if (xbar) {
+    // bbar = A^{-1} xbar by the two substitution sweeps on the factor
+    if (cudaMemcpyAsync(bbar, xbar, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+      return BCHOL_ERR_CUDA;
+    int l2 = 0;
+    if (launch_solve(n, kk, 1, ab, ldab, bbar, n, ws + kStatusBytes, &l2, h->stream) != cudaSuccess) {
+      cudaGetLastError();
+      return BCHOL_ERR_CUDA;
+    }
+    launches += l2;
+  }
+  if (launch_backward(n, kk, b, ab, ldab, xbar ? x : nullptr, xbar ? bbar : nullptr, ldbar, abar, ldabar,
+                      ws + kStatusBytes, status, (uint64_t)h->wait_ms * 1000000ull,
+                      h->ctas_per_sm ? h->ctas_per_sm : auto_ctas_per_sm(kk), h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return BCHOL_ERR_CUDA;
+  }
+  h->last_launches = launches + 3;
+  return BCHOL_OK;
+}
+
+bchol_status_t bchol_solve_mixed(bchol_handle_t h, int n, int k, int nrhs, const double* ab, int ldab,
+                                 const double* b, int ldb, double* x, int ldx, int max_iter, double tol,
+                                 int* info_dev, int* iters, double* resid, double* corr) {
+  if (!h || n < 1 || k < 0 || nrhs < 1 || ldab < k + 1 || ldb < n || ldx < n || !ab || !b || !x || !info_dev ||
+      max_iter < 0 || !(tol >= 0.0) || !iters || !resid || !corr)
+    return BCHOL_ERR_ARG;
+  h->last_launches = 0;
+  const int kk = k > n - 1 ? n - 1 : k;
+  const int tile = h->tile ? h->tile : auto_tile(kk);
+  char* ws = nullptr;
+  bchol_status_t rc = get_workspace(h, kStatusBytes + mixed_workspace_bytes(n, kk, nrhs, tile), &ws);
+  if (rc != BCHOL_OK) return rc;
+  int* status = reinterpret_cast<int*>(ws);
+  h->last_status = status;
+  int launches = 0;
+  const int r = mixed_solve(n, kk, nrhs, ab, ldab, b, ldb, x, ldx, max_iter, tol, info_dev, tile,
+                            h->ctas_per_sm ? h->ctas_per_sm : auto_ctas_per_sm(kk), ws + kStatusBytes, status,
+                            (uint64_t)h->wait_ms * 1000000ull, h->stream, iters, resid, corr, &launches);
+  h->last_launches = launches;
+  if (r != BCHOL_OK) cudaGetLastError();
+  int st = 0;
+  if (r == BCHOL_OK && cudaMemcpy(&st, status, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && st != 0)
+    return BCHOL_ERR_TIMEOUT;
+  return static_cast<bchol_status_t>(r);
+}
+
 bchol_status_t bchol_batch_run(bchol_handle_t h, bchol_batch_t batch) {
   if (!h || !batch) return BCHOL_ERR_ARG;
   h->last_launches = 0;

@@ -18,6 +18,7 @@ struct FactorPlan {
   long long Treg = 0;          // tasks per such block: 2p + 1 + p(p-1)/2
   unsigned long long total = 0;  // tasks of the whole factorization
   size_t flag_count = 0;       // ints of ready flags: S*(p+1)
+  bool f32_update = false;     // mixed precision: trailing updates accumulated in FP32
 };
 
 FactorPlan make_factor_plan(int n, int k, int b);
@@ -35,8 +36,25 @@ int solve_block(int k);
 size_t solve_workspace_bytes(int n, int k);
 cudaError_t launch_solve(int n, int k, int nrhs, const double* ab, long long ldab, double* b, long long ldb,
                          void* ws, int* launches, cudaStream_t stream);
+// The same sweeps with FP32 arithmetic (FP64 band and right-hand sides in memory).
+cudaError_t launch_solve_f32(int n, int k, int nrhs, const double* ab, long long ldab, double* b, long long ldb,
+                             void* ws, int* launches, cudaStream_t stream);
 
 int num_sms();
+
+// Adjoint (selinv.cu): band of A^{-1} by selected inversion and the band gradient.
+size_t selinv_workspace_bytes(int n, int k, int b);
+cudaError_t launch_backward(int n, int k, int b, const double* L, long long ldl, const double* x, const double* bbar,
+                            double ldbar, double* g, long long ldg, void* ws, int* status, uint64_t wait_ns,
+                            int ctas_per_sm, cudaStream_t stream);
+cudaError_t launch_logdet(const double* ab, long long ldab, int n, double* out, cudaStream_t stream);
+
+// Mixed-precision factor + FP64 iterative refinement (mixed.cu).
+size_t mixed_workspace_bytes(int n, int k, int nrhs, int tile);
+int mixed_solve(int n, int k, int nrhs, const double* ab, long long ldab, const double* b, long long ldb, double* x,
+                long long ldx, int max_iter, double tol, int* info_dev, int tile, int ctas_per_sm, void* ws,
+                int* status, uint64_t wait_ns, cudaStream_t stream, int* iters_out, double* resid_out,
+                double* corr_out, int* launches_out);
 
 }  // namespace bchol
 

@@ -28,7 +28,7 @@
 
 namespace bchol {
 
-template <int B>
+template <int B, bool F32>
 __global__ void __launch_bounds__(kThreads, 2) factor_kernel(FactorArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<B>& sm = *reinterpret_cast<Smem<B>*>(smem_raw);
@@ -49,6 +49,8 @@ __global__ void __launch_bounds__(kThreads, 2) factor_kernel(FactorArgs a) {
       ok = task_potrf<B>(a, s, sm, &s_flag);
     else if (type == kTrsm)
       ok = task_trsm<B>(a, I, s, sm, &s_flag);
+    else if (F32)
+      ok = task_upd_f32<B>(a, I, J, s, sm, &s_flag);
     else
       ok = task_upd<B>(a, I, J, s, sm, &s_flag);
     if (!ok) break;
@@ -77,19 +79,20 @@ FactorPlan make_factor_plan(int n, int k, int b) {
 
 size_t factor_workspace_bytes(const FactorPlan& P) { return 256 + P.flag_count * sizeof(int); }
 
-template <int B>
+template <int B, bool F32>
 static cudaError_t launch_b(const FactorArgs& a, int ctas_per_sm, cudaStream_t stream) {
   const size_t smem = sizeof(Smem<B>);
-  cudaError_t e = cudaFuncSetAttribute(factor_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e =
+      cudaFuncSetAttribute(factor_kernel<B, F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, factor_kernel<B>, kThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, factor_kernel<B, F32>, kThreads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
   long long grid = (long long)per_sm * num_sms();
   if ((unsigned long long)grid > a.total) grid = (long long)a.total;
-  factor_kernel<B><<<(unsigned)grid, kThreads, smem, stream>>>(a);
+  factor_kernel<B, F32><<<(unsigned)grid, kThreads, smem, stream>>>(a);
   return cudaGetLastError();
 }
 
@@ -117,10 +120,18 @@ cudaError_t launch_factor(const FactorPlan& P, double* ab, long long ldab, int* 
   a.stall = -1;
   if (stall_I >= 0 && stall_J >= 0 && stall_I < P.S && stall_J <= stall_I && stall_I - stall_J <= P.p)
     a.stall = stall_J * (P.p + 1) + (stall_I - stall_J);
+  if (P.f32_update) {
+    switch (P.b) {
+      case 16: return launch_b<16, true>(a, ctas_per_sm, stream);
+      case 32: return launch_b<32, true>(a, ctas_per_sm, stream);
+      case 64: return launch_b<64, true>(a, ctas_per_sm, stream);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (P.b) {
-    case 16: return launch_b<16>(a, ctas_per_sm, stream);
-    case 32: return launch_b<32>(a, ctas_per_sm, stream);
-    case 64: return launch_b<64>(a, ctas_per_sm, stream);
+    case 16: return launch_b<16, false>(a, ctas_per_sm, stream);
+    case 32: return launch_b<32, false>(a, ctas_per_sm, stream);
+    case 64: return launch_b<64, false>(a, ctas_per_sm, stream);
     default: return cudaErrorInvalidValue;
   }
 }

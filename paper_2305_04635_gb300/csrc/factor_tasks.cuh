@@ -232,5 +232,71 @@ __device__ bool task_upd(const FactorArgs& a, int I, int J, int s, Smem<B>& sm, 
   return true;
 }
 
+// ------------------------------------------------------------ UPD, FP32 update
+// The mixed-precision form of UPD: the two panel tiles are rounded to FP32,
+// their product L_Is L_Js^T is accumulated in FP32 (FFMA), and the FP64 tile
+// is updated by that product, A_IJ -= (double) P.  POTRF and TRSM stay FP64.
+template <int B>
+__device__ bool task_upd_f32(const FactorArgs& a, int I, int J, int s, Smem<B>& sm, int* s_flag) {
+  constexpr int R = B / 16;
+  const int tid = threadIdx.x;
+  const int s0I = first_step(a, I);
+  if (tid == 0) {
+    bool ok = wait_tile(a, I, s, s - s0I + 1);
+    if (ok && J != I) ok = wait_tile(a, J, s, s - first_step(a, J) + 1);
+    if (ok) ok = wait_tile(a, I, J, s - s0I);
+    *s_flag = ok;
+  }
+  __syncthreads();
+  if (!*s_flag) return false;
+  float* fA = reinterpret_cast<float*>(sm.t0);
+  float* fB = reinterpret_cast<float*>(sm.t1);
+  for (int idx = tid; idx < B * B; idx += kThreads) {
+    const int i = idx % B, l = idx / B;
+    const int gl = s * B + l;
+    int gi = I * B + i, d = gi - gl;
+    fA[l * B + i] = (gi < a.n && d >= 0 && d <= a.k) ? (float)__ldcg(a.ab + d + (long long)gl * a.ldab) : 0.0f;
+    if (J != I) {
+      gi = J * B + i;
+      d = gi - gl;
+      fB[l * B + i] = (gi < a.n && d >= 0 && d <= a.k) ? (float)__ldcg(a.ab + d + (long long)gl * a.ldab) : 0.0f;
+    }
+  }
+  const float* fBr = (J != I) ? fB : fA;
+  const int ty = tid / 16, tx = tid % 16;
+  const bool diag = (I == J);
+  float acc[R][R];
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int c = 0; c < R; ++c) acc[r][c] = 0.0f;
+  __syncthreads();
+#pragma unroll 4
+  for (int l = 0; l < B; ++l) {
+    float av[R], bv[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) av[r] = fA[l * B + ty + 16 * r];
+#pragma unroll
+    for (int c = 0; c < R; ++c) bv[c] = fBr[l * B + tx + 16 * c];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int c = 0; c < R; ++c)
+        if (!(diag && r < c)) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int c = 0; c < R; ++c) {
+      const int gi = I * B + ty + 16 * r, gj = J * B + tx + 16 * c;
+      const int d = gi - gj;
+      if (gi < a.n && d >= 0 && d <= a.k) {
+        double* p = a.ab + d + (long long)gj * a.ldab;
+        *p = __ldcg(p) - (double)acc[r][c];
+      }
+    }
+  publish(&a.flags[fidx(a, I, J)], s - s0I + 1);
+  return true;
+}
 
 }  // namespace bchol

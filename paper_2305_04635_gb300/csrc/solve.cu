@@ -27,7 +27,8 @@ namespace cg = cooperative_groups;
 namespace bchol {
 
 constexpr int kSB = 32;        // solve block
-constexpr int kNRC = 8;        // right-hand sides per pass
+constexpr int kNRC = 8;        // right-hand sides per pass, FP64 sweeps
+constexpr int kNRC32 = 16;     // right-hand sides per pass, FP32 sweeps
 constexpr int kSThreads = 256;
 constexpr int kSWarps = kSThreads / 32;
 constexpr int kQ = kSB / kSWarps;   // columns per warp in a 32 x 32 product
@@ -133,19 +134,25 @@ struct SolveArgs {
 // parts of the union.  pfs/lvs are per-thread prefetch slots, double-buffered
 // by chain position, filled with cp.async: unlike plain loads, these copies do
 // not hold up the release of the cluster barrier at the end of a round.
-template <int NW>
+// T is the arithmetic type of the sweeps: double for bchol_solve, float for
+// the correction solves of the mixed-precision refinement.  Band tiles and
+// the prepared blocks are always read as FP64 and rounded to T when used.
+template <int NW, typename T, int NRC>
 struct SolveSmem {
   union {
-    double part[2][NW][kNRC][kSB];        // leader: workers' shares for the next two blocks
+    T part[2][NW][NRC][kSB];             // leader: workers' shares for the next two blocks
     struct {
       double pfs[2][kMaxT][kQ][kSThreads];  // worker: far band tiles
-      double ring[kRing][kNRC][kSB];        // worker: solution blocks pushed by the leader
+      T ring[kRing][NRC][kSB];             // worker: solution blocks pushed by the leader
     } w;
   } u;
   double lvs[2][kQ][kSThreads];           // L_TT^{-1} (worker) or M_T / N_T (leader)
-  double red[kSWarps][kNRC][kSB];
-  double vec[kNRC][kSB];                  // leader: last chain block; worker: its partial sum
+  T red[kSWarps][NRC][kSB];
+  T vec[NRC][kSB];                       // leader: last chain block; worker: its partial sum
 };
+
+__device__ __forceinline__ double fmat(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmat(float a, float b, float c) { return fmaf(a, b, c); }
 
 __device__ __forceinline__ void cp_async8(double* dst, const double* src, bool valid) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -156,21 +163,21 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // Balanced-tree sum of N values p[0], p[stride], ... (short dependency chains).
-template <int N>
-__device__ __forceinline__ double tree_sum(const double* p, int stride) {
+template <int N, typename T>
+__device__ __forceinline__ T tree_sum(const T* p, int stride) {
   if constexpr (N == 1) {
     return p[0];
   } else {
     constexpr int H = N / 2;
-    return tree_sum<H>(p, stride) + tree_sum<N - H>(p + H * stride, stride);
+    return tree_sum<H, T>(p, stride) + tree_sum<N - H, T>(p + H * stride, stride);
   }
 }
 
 // Cross-warp sum: each warp's per-lane values acc[r] (r < nr) -> out[r][lane] (32*nr threads write).
-template <int NW>
-__device__ __forceinline__ void warp_sum_rows(const double (&acc)[kNRC], int nr, SolveSmem<NW>& sm, int w, int lane) {
+template <int NW, typename T, int NRC>
+__device__ __forceinline__ void warp_sum_rows(const T (&acc)[NRC], int nr, SolveSmem<NW, T, NRC>& sm, int w, int lane) {
 #pragma unroll
-  for (int r = 0; r < kNRC; ++r)
+  for (int r = 0; r < NRC; ++r)
     if (r < nr) sm.red[w][r][lane] = acc[r];
   __syncthreads();
 }
@@ -191,22 +198,22 @@ __device__ __forceinline__ const double* tile_addr(const SolveArgs& a, bool fwd,
   return *ok ? a.ab + d + (long long)gj * a.ldab : a.ab;
 }
 
-template <int CL>
+template <int CL, typename VT, int NRC>
 __global__ void __launch_bounds__(kSThreads, 1) solve_kernel(SolveArgs a) {
   constexpr int NW = CL - 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  SolveSmem<NW>& sm = *reinterpret_cast<SolveSmem<NW>*>(smem_raw);
+  SolveSmem<NW, VT, NRC>& sm = *reinterpret_cast<SolveSmem<NW, VT, NRC>*>(smem_raw);
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  SolveSmem<NW>* leader = cluster.map_shared_rank(&sm, 0);
+  SolveSmem<NW, VT, NRC>* leader = cluster.map_shared_rank(&sm, 0);
 
-  for (int c0 = 0; c0 < a.nrhs; c0 += kNRC) {
-    const int nr = min(kNRC, a.nrhs - c0);
+  for (int c0 = 0; c0 < a.nrhs; c0 += NRC) {
+    const int nr = min(NRC, a.nrhs - c0);
     double* bc = a.b + (long long)c0 * a.ldb;
     for (int sweep = 0; sweep < 2; ++sweep) {
       const bool fwd = (sweep == 0);
-      for (int idx = tid; idx < kNRC * kSB; idx += kSThreads) (&sm.vec[0][0])[idx] = 0.0;
+      for (int idx = tid; idx < NRC * kSB; idx += kSThreads) (&sm.vec[0][0])[idx] = VT(0);
       // Registers prefetched one round ahead: the worker's far tiles and L_TT^{-1} (or its
       // transpose), or the leader's coupling block M_T / N_T.  Lane = output row i, column
       // c = w + 8q of the 32 x 32 product.
@@ -248,57 +255,59 @@ __global__ void __launch_bounds__(kSThreads, 1) solve_kernel(SolveArgs a) {
         const int T = fwd ? pos : a.S - 1 - pos;
         const int jlo = fwd ? max(0, T - a.P) : T + 2;
         const int jhi = fwd ? T - 2 : min(a.S - 1, T + a.P);
-        double acc[kNRC];
+        VT acc[NRC];
 #pragma unroll
-        for (int r = 0; r < kNRC; ++r) acc[r] = 0.0;
+        for (int r = 0; r < NRC; ++r) acc[r] = VT(0);
         const int buf = pos & 1;
-        cp_async_wait_all();
         int J = jlo + ((rank - 1) - (jlo % NW) + NW) % NW;
         for (int t = 0; J <= jhi; ++t, J += NW) {
-          const double* ring = &sm.u.w.ring[(J / NW) % kRing][0][0];
+          const VT* ring = &sm.u.w.ring[(J / NW) % kRing][0][0];
 #pragma unroll
           for (int q = 0; q < kQ; ++q) {
             const int c = w + kSWarps * q;
-            const double m = (t < kMaxT) ? sm.u.w.pfs[buf][t][q][tid] : tile_entry(a, fwd, T, J, lane, c);
+            const VT m = (VT)((t < kMaxT) ? sm.u.w.pfs[buf][t][q][tid] : tile_entry(a, fwd, T, J, lane, c));
             const int gc = J * kSB + c;
 #pragma unroll
-            for (int r = 0; r < kNRC; ++r) {
+            for (int r = 0; r < NRC; ++r) {
               if (r < nr) {
-                const double v = a.use_ring ? ring[r * kSB + c]
-                                            : (gc < a.n ? __ldcg(bc + gc + (long long)r * a.ldb) : 0.0);
-                acc[r] = fma(m, v, acc[r]);
+                const VT v = a.use_ring ? ring[r * kSB + c]
+                                       : (VT)(gc < a.n ? __ldcg(bc + gc + (long long)r * a.ldb) : 0.0);
+                acc[r] = fmat(m, v, acc[r]);
               }
             }
           }
         }
-        warp_sum_rows<NW>(acc, nr, sm, w, lane);
-        if (tid < nr * kSB) {
-          const int r = tid / kSB, i = tid % kSB;
-          double s = tree_sum<kSWarps>(&sm.red[0][r][i], kNRC * kSB);
-          if (rank == 1 && T * kSB + i < a.n) s -= __ldcg(bc + T * kSB + i + (long long)r * a.ldb);
+        warp_sum_rows<NW, VT, NRC>(acc, nr, sm, w, lane);
+        for (int idx = tid; idx < nr * kSB; idx += kSThreads) {
+          const int r = idx / kSB, i = idx % kSB;
+          VT s = tree_sum<kSWarps, VT>(&sm.red[0][r][i], NRC * kSB);
+          if (rank == 1 && T * kSB + i < a.n) s -= (VT)__ldcg(bc + T * kSB + i + (long long)r * a.ldb);
           sm.vec[r][i] = s;
         }
         __syncthreads();
 #pragma unroll
-        for (int r = 0; r < kNRC; ++r) {
-          acc[r] = 0.0;
+        for (int r = 0; r < NRC; ++r) {
+          acc[r] = VT(0);
           if (r < nr) {
 #pragma unroll
-            for (int q = 0; q < kQ; ++q) acc[r] = fma(sm.lvs[buf][q][tid], sm.vec[r][w + kSWarps * q], acc[r]);
+            for (int q = 0; q < kQ; ++q) acc[r] = fmat((VT)sm.lvs[buf][q][tid], sm.vec[r][w + kSWarps * q], acc[r]);
           }
         }
-        warp_sum_rows<NW>(acc, nr, sm, w, lane);
-        if (tid < nr * kSB) {
-          const int r = tid / kSB, i = tid % kSB;
-          leader->u.part[T & 1][rank - 1][r][i] = tree_sum<kSWarps>(&sm.red[0][r][i], kNRC * kSB);
+        warp_sum_rows<NW, VT, NRC>(acc, nr, sm, w, lane);
+        for (int idx = tid; idx < nr * kSB; idx += kSThreads) {
+          const int r = idx / kSB, i = idx % kSB;
+          leader->u.part[T & 1][rank - 1][r][i] = tree_sum<kSWarps, VT>(&sm.red[0][r][i], NRC * kSB);
         }
       };
 
       // round -1: the workers' shares for the first chain block
+      // Prefetches are issued one round before they are used, at the start of a
+      // round, so that the HBM latency overlaps a whole round.
       prefetch(0);
       if (rank != 0) {
-        worker_step(0);
+        cp_async_wait_all();
         prefetch(1);
+        worker_step(0);
       }
       cluster.sync();
       for (int pos = 0; pos < a.S; ++pos) {
@@ -307,31 +316,32 @@ __global__ void __launch_bounds__(kSThreads, 1) solve_kernel(SolveArgs a) {
           // block T = -(M_T or N_T) * previous block - sum of the workers' shares
           const int buf = pos & 1;
           cp_async_wait_all();
-          double acc[kNRC];
+          prefetch(pos + 1);
+          VT acc[NRC];
 #pragma unroll
-          for (int r = 0; r < kNRC; ++r) {
-            acc[r] = 0.0;
+          for (int r = 0; r < NRC; ++r) {
+            acc[r] = VT(0);
             if (r < nr) {
 #pragma unroll
-              for (int q = 0; q < kQ; ++q) acc[r] = fma(sm.lvs[buf][q][tid], sm.vec[r][w + kSWarps * q], acc[r]);
+              for (int q = 0; q < kQ; ++q) acc[r] = fmat((VT)sm.lvs[buf][q][tid], sm.vec[r][w + kSWarps * q], acc[r]);
             }
           }
-          warp_sum_rows<NW>(acc, nr, sm, w, lane);
-          if (tid < nr * kSB) {
-            const int r = tid / kSB, i = tid % kSB, gi = T * kSB + i;
-            const double y = -(tree_sum<kSWarps>(&sm.red[0][r][i], kNRC * kSB) +
-                               tree_sum<NW>(&sm.u.part[T & 1][0][r][i], kNRC * kSB));
+          warp_sum_rows<NW, VT, NRC>(acc, nr, sm, w, lane);
+          for (int idx = tid; idx < nr * kSB; idx += kSThreads) {
+            const int r = idx / kSB, i = idx % kSB, gi = T * kSB + i;
+            const VT y = -(tree_sum<kSWarps, VT>(&sm.red[0][r][i], NRC * kSB) +
+                           tree_sum<NW, VT>(&sm.u.part[T & 1][0][r][i], NRC * kSB));
             sm.vec[r][i] = y;
-            if (gi < a.n) bc[gi + (long long)r * a.ldb] = y;
+            if (gi < a.n) bc[gi + (long long)r * a.ldb] = (double)y;
             if (a.use_ring) {
-              SolveSmem<NW>* owner = cluster.map_shared_rank(&sm, (T % NW) + 1);
+              SolveSmem<NW, VT, NRC>* owner = cluster.map_shared_rank(&sm, (T % NW) + 1);
               owner->u.w.ring[(T / NW) % kRing][r][i] = y;
             }
           }
-          prefetch(pos + 1);
         } else if (pos + 1 < a.S) {
-          worker_step(pos + 1);
+          cp_async_wait_all();
           prefetch(pos + 2);
+          worker_step(pos + 1);
         }
         cluster.sync();
       }
@@ -339,15 +349,15 @@ __global__ void __launch_bounds__(kSThreads, 1) solve_kernel(SolveArgs a) {
   }
 }
 
-template <int CL>
+template <int CL, typename VT, int NRC>
 static cudaError_t launch_cluster(const SolveArgs& a0, cudaStream_t stream, bool* fits) {
   SolveArgs a = a0;
   a.use_ring = (a.P <= (CL - 1) * (kRing - 1)) ? 1 : 0;
-  const size_t smem = sizeof(SolveSmem<CL - 1>);
-  cudaError_t e = cudaFuncSetAttribute(solve_kernel<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = sizeof(SolveSmem<CL - 1, VT, NRC>);
+  cudaError_t e = cudaFuncSetAttribute(solve_kernel<CL, VT, NRC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (CL > 8) {
-    e = cudaFuncSetAttribute(solve_kernel<CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(solve_kernel<CL, VT, NRC>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) {
       cudaGetLastError();
       *fits = false;
@@ -367,18 +377,19 @@ static cudaError_t launch_cluster(const SolveArgs& a0, cudaStream_t stream, bool
   cfg.attrs = at;
   cfg.numAttrs = 1;
   int clusters = 0;
-  e = cudaOccupancyMaxActiveClusters(&clusters, solve_kernel<CL>, &cfg);
+  e = cudaOccupancyMaxActiveClusters(&clusters, solve_kernel<CL, VT, NRC>, &cfg);
   if (e != cudaSuccess || clusters < 1) {
     cudaGetLastError();
     *fits = false;
     return cudaSuccess;
   }
   *fits = true;
-  return cudaLaunchKernelEx(&cfg, solve_kernel<CL>, a);
+  return cudaLaunchKernelEx(&cfg, solve_kernel<CL, VT, NRC>, a);
 }
 
-cudaError_t launch_solve(int n, int k, int nrhs, const double* ab, long long ldab, double* b, long long ldb, void* ws,
-                         int* launches, cudaStream_t stream) {
+template <typename VT, int NRC>
+static cudaError_t launch_solve_t(int n, int k, int nrhs, const double* ab, long long ldab, double* b, long long ldb,
+                                  void* ws, int* launches, cudaStream_t stream) {
   *launches = 0;
   if (n <= 0 || nrhs <= 0) return cudaSuccess;
   if (k > n - 1) k = n - 1;
@@ -394,11 +405,21 @@ cudaError_t launch_solve(int n, int k, int nrhs, const double* ab, long long lda
   *launches = 1;
   SolveArgs a{ab, ldab, n, k, S, P, b, ldb, nrhs, linv, mfw, nbw, 1};
   bool fits = false;
-  e = launch_cluster<16>(a, stream, &fits);
-  if (e == cudaSuccess && !fits) e = launch_cluster<8>(a, stream, &fits);
+  e = launch_cluster<16, VT, NRC>(a, stream, &fits);
+  if (e == cudaSuccess && !fits) e = launch_cluster<8, VT, NRC>(a, stream, &fits);
   if (e == cudaSuccess && !fits) e = cudaErrorInvalidConfiguration;
   if (e == cudaSuccess) *launches = 2;
   return e;
+}
+
+cudaError_t launch_solve(int n, int k, int nrhs, const double* ab, long long ldab, double* b, long long ldb, void* ws,
+                         int* launches, cudaStream_t stream) {
+  return launch_solve_t<double, kNRC>(n, k, nrhs, ab, ldab, b, ldb, ws, launches, stream);
+}
+
+cudaError_t launch_solve_f32(int n, int k, int nrhs, const double* ab, long long ldab, double* b, long long ldb,
+                             void* ws, int* launches, cudaStream_t stream) {
+  return launch_solve_t<float, kNRC32>(n, k, nrhs, ab, ldab, b, ldb, ws, launches, stream);
 }
 
 }  // namespace bchol
