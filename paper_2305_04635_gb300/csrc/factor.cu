@@ -47,6 +47,8 @@ __global__ void __launch_bounds__(kThreads, 2) factor_kernel(FactorArgs a) {
     bool ok;
     if (type == kPotrf)
       ok = task_potrf<B>(a, s, sm, &s_flag);
+    else if (type == kTrsm && F32)
+      ok = task_trsm_f32<B>(a, I, s, sm, &s_flag);
     else if (type == kTrsm)
       ok = task_trsm<B>(a, I, s, sm, &s_flag);
     else if (F32)

@@ -232,6 +232,66 @@ __device__ bool task_upd(const FactorArgs& a, int I, int J, int s, Smem<B>& sm, 
   return true;
 }
 
+// ------------------------------------------------------------ TRSM, FP32
+// The mixed-precision form of TRSM: X = A_Is L_ss^{-T} with both tiles
+// rounded to FP32 and the substitution in FP32; the result is stored in the
+// FP64 band.  (The diagonal POTRF stays FP64; refinement of the solve
+// recovers FP64 accuracy.)
+template <int B>
+__device__ bool task_trsm_f32(const FactorArgs& a, int I, int s, Smem<B>& sm, int* s_flag) {
+  constexpr int TPR = kThreads / B;
+  constexpr int R = B / TPR;
+  __shared__ float s_rinv32[B];
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    bool ok = wait_tile(a, s, s, s - first_step(a, s) + 1);
+    if (ok) ok = wait_tile(a, I, s, s - first_step(a, I));
+    *s_flag = ok;
+  }
+  __syncthreads();
+  if (!*s_flag) return false;
+  float* fX = reinterpret_cast<float*>(sm.t0);
+  float* fL = reinterpret_cast<float*>(sm.t1);
+  for (int idx = tid; idx < B * B; idx += kThreads) {
+    const int i = idx % B, j = idx / B;
+    int gi = I * B + i, gj = s * B + j, d = gi - gj;
+    fX[j * B + i] = (gi < a.n && d >= 0 && d <= a.k) ? (float)__ldcg(a.ab + d + (long long)gj * a.ldab) : 0.0f;
+    gi = s * B + i;
+    d = gi - gj;
+    fL[j * B + i] = (gi < a.n && d >= 0 && d <= a.k) ? (float)__ldcg(a.ab + d + (long long)gj * a.ldab) : 0.0f;
+  }
+  __syncthreads();
+  const int jmax = min(B, a.n - s * B);
+  if (tid < B) s_rinv32[tid] = (tid < jmax) ? 1.0f / fL[tid * B + tid] : 0.0f;
+  const int i = tid / TPR, sub = tid % TPR;
+  float acc[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) acc[q] = fX[(sub + q * TPR) * B + i];
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < B; ++j) {
+    const int owner = j % TPR, qj = j / TPR;
+    float x = 0.0f;
+    if (sub == owner) {
+      x = acc[qj] * s_rinv32[j];
+      acc[qj] = x;
+    }
+    x = __shfl_sync(0xffffffffu, x, owner, TPR);
+#pragma unroll
+    for (int q = qj; q < R; ++q) {
+      const int l = sub + q * TPR;
+      if (l > j) acc[q] = fmaf(-x, fL[j * B + l], acc[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const int gi = I * B + i, gj = s * B + sub + q * TPR, d = gi - gj;
+    if (gi < a.n && d >= 0 && d <= a.k) a.ab[d + (long long)gj * a.ldab] = (double)acc[q];
+  }
+  publish(&a.flags[fidx(a, I, s)], s - first_step(a, I) + 1);
+  return true;
+}
+
 // ------------------------------------------------------------ UPD, FP32 update
 // The mixed-precision form of UPD: the two panel tiles are rounded to FP32,
 // their product L_Is L_Js^T is accumulated in FP32 (FFMA), and the FP64 tile

@@ -128,6 +128,7 @@ struct SolveArgs {
   const double* mfw;
   const double* nbw;
   int use_ring;   // far solution blocks come from the pushed ring (else from global memory)
+  int rhs_per;    // right-hand-side columns per cluster (clusters split the columns)
 };
 
 // Shared-memory layout (doubles).  The leader and the workers use different
@@ -208,8 +209,12 @@ __global__ void __launch_bounds__(kSThreads, 1) solve_kernel(SolveArgs a) {
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   SolveSmem<NW, VT, NRC>* leader = cluster.map_shared_rank(&sm, 0);
 
-  for (int c0 = 0; c0 < a.nrhs; c0 += NRC) {
-    const int nr = min(NRC, a.nrhs - c0);
+  // Clusters split the right-hand sides: cluster blockIdx.x / CL takes columns
+  // [cid * rhs_per, (cid + 1) * rhs_per); the clusters run side by side.
+  const int cid = blockIdx.x / CL;
+  const int cbeg = cid * a.rhs_per, cend = min(a.nrhs, cbeg + a.rhs_per);
+  for (int c0 = cbeg; c0 < cend; c0 += NRC) {
+    const int nr = min(NRC, cend - c0);
     double* bc = a.b + (long long)c0 * a.ldb;
     for (int sweep = 0; sweep < 2; ++sweep) {
       const bool fwd = (sweep == 0);
@@ -350,7 +355,7 @@ __global__ void __launch_bounds__(kSThreads, 1) solve_kernel(SolveArgs a) {
 }
 
 template <int CL, typename VT, int NRC>
-static cudaError_t launch_cluster(const SolveArgs& a0, cudaStream_t stream, bool* fits) {
+static cudaError_t launch_cluster(const SolveArgs& a0, cudaStream_t stream, bool* fits, bool need_all) {
   SolveArgs a = a0;
   a.use_ring = (a.P <= (CL - 1) * (kRing - 1)) ? 1 : 0;
   const size_t smem = sizeof(SolveSmem<CL - 1, VT, NRC>);
@@ -378,11 +383,15 @@ static cudaError_t launch_cluster(const SolveArgs& a0, cudaStream_t stream, bool
   cfg.numAttrs = 1;
   int clusters = 0;
   e = cudaOccupancyMaxActiveClusters(&clusters, solve_kernel<CL, VT, NRC>, &cfg);
-  if (e != cudaSuccess || clusters < 1) {
+  if (e != cudaSuccess || clusters < 1 || (need_all && clusters < a.nrhs)) {
     cudaGetLastError();
     *fits = false;
     return cudaSuccess;
   }
+  // as many clusters as fit at once, each with an equal share of the columns
+  a.rhs_per = (a.nrhs + clusters - 1) / clusters;
+  const int groups = (a.nrhs + a.rhs_per - 1) / a.rhs_per;
+  cfg.gridDim = dim3(CL * groups);
   *fits = true;
   return cudaLaunchKernelEx(&cfg, solve_kernel<CL, VT, NRC>, a);
 }
@@ -403,10 +412,14 @@ static cudaError_t launch_solve_t(int n, int k, int nrhs, const double* ab, long
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   *launches = 1;
-  SolveArgs a{ab, ldab, n, k, S, P, b, ldb, nrhs, linv, mfw, nbw, 1};
+  SolveArgs a{ab, ldab, n, k, S, P, b, ldb, nrhs, linv, mfw, nbw, 1, nrhs};
   bool fits = false;
-  e = launch_cluster<16, VT, NRC>(a, stream, &fits);
-  if (e == cudaSuccess && !fits) e = launch_cluster<8, VT, NRC>(a, stream, &fits);
+  // One column per cluster when 16-CTA clusters can cover all of them; else 8-CTA
+  // clusters (more of them fit); else 16-CTA clusters with several columns each.
+  e = launch_cluster<16, VT, NRC>(a, stream, &fits, true);
+  if (e == cudaSuccess && !fits) e = launch_cluster<8, VT, NRC>(a, stream, &fits, true);
+  if (e == cudaSuccess && !fits) e = launch_cluster<16, VT, NRC>(a, stream, &fits, false);
+  if (e == cudaSuccess && !fits) e = launch_cluster<8, VT, NRC>(a, stream, &fits, false);
   if (e == cudaSuccess && !fits) e = cudaErrorInvalidConfiguration;
   if (e == cudaSuccess) *launches = 2;
   return e;
