@@ -260,6 +260,195 @@ def run_ours(args, rank: int, world: int, dev: int):
     return out, data
 
 
+def _ev():
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _colmajor(B: np.ndarray) -> torch.Tensor:
+    """(n, nrhs) float64 device tensor with column-major strides (ldb = n)."""
+    return torch.from_numpy(np.ascontiguousarray(B.T)).cuda().T
+
+
+def next_batched(count: int = 512, reps: int = 3) -> dict:
+    """512 independent systems, n log-uniform in [1e3, 5e4], k log-uniform in [50, 400], 4 RHS each:
+    one graph-captured batched launch (autotuned tile and CTAs per SM) against a loop of the plain
+    per-matrix factor + solve on the same stream."""
+    import paper_2305_04635_gb300 as bchol
+    from paper_2305_04635_gb300 import autotune
+
+    t0 = time.perf_counter()
+    ns, ks = bandgen.batch_shapes(count, seed=0)
+    pr, bpr = [], []
+    for m, (n, k) in enumerate(zip(ns, ks)):
+        A = bandgen.band_product(bandgen.l0_band(n, k, 0, "log1e3", matrix_id=m), k)
+        pr.append(bchol.band_from_numpy(A))
+        bpr.append(_colmajor(bandgen.rhs(n, 4, 0, m)))
+    gen_s = time.perf_counter() - t0
+    work = [p.clone() for p in pr]
+    bw = [b.clone() for b in bpr]
+    F = sum(flops_eq1(n, k) for n, k in zip(ns, ks))
+
+    def restore():
+        for w, p in zip(work, pr):
+            w.copy_(p)
+        for w, p in zip(bw, bpr):
+            w.copy_(p)
+        torch.cuda.synchronize()
+
+    stream = torch.cuda.Stream()
+    h = bchol.Handle(stream=stream)
+    # plain loop: one warm-up pass over the first systems, then one timed pass over all of them
+    with torch.cuda.stream(stream):
+        for w, k, b in list(zip(work, ks, bw))[:16]:
+            bchol.factor(w, k, handle=h)
+            bchol.solve(w, k, b, handle=h)
+    restore()
+    infos = torch.zeros(count, dtype=torch.int32, device="cuda")
+    e0, e1 = _ev()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for m, (w, k, b) in enumerate(zip(work, ks, bw)):
+            bchol.factor(w, k, info=infos[m:m + 1], handle=h)
+            bchol.solve(w, k, b, handle=h)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    if int(infos.abs().sum()) != 0:
+        raise RuntimeError("batched leg: a plain factorization failed")
+    x_plain = [b.clone() for b in bw]
+
+    t1 = time.perf_counter()
+    tile, cps = autotune.tune_batch(pr, ks, bpr, handle=h)
+    tune_s = time.perf_counter() - t1
+    batch = bchol.Batch(work, ks, bw, tile=tile, ctas_per_sm=cps)
+    restore()
+    with torch.cuda.stream(stream):
+        batch.run(h)                      # workspace set-up outside the capture
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        batch.run(h)
+    times = []
+    for _ in range(reps + 1):
+        restore()
+        e0, e1 = _ev()
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    batched_ms = statistics.median(times[1:])
+    if batch.info.cpu().tolist() != [0] * count:
+        raise RuntimeError("batched leg: a batched factorization failed")
+    diff = max(float(torch.linalg.norm(a - c) / torch.linalg.norm(c)) for a, c in zip(bw, x_plain))
+    batch.close()
+    return {"workload": f"{count} systems, n log-uniform [1e3,5e4], k log-uniform [50,400], 4 RHS, "
+                        "L0 diag log-uniform [1,1e3]",
+            "flops_eq1": F, "plain_loop_ms": round(plain_ms, 3), "batched_ms": round(batched_ms, 3),
+            "speedup_vs_plain": round(plain_ms / batched_ms, 3),
+            "batched_gflops_eq1": round(F / batched_ms / 1e6, 2),
+            "factorizations_per_s": round(count / batched_ms * 1e3, 2),
+            "plain_factorizations_per_s": round(count / plain_ms * 1e3, 2),
+            "tile": tile, "ctas_per_sm": cps, "cuda_graph": True,
+            "max_rel_diff_x_vs_plain": diff, "gen_s": round(gen_s, 1), "tune_s": round(tune_s, 1)}
+
+
+def next_mixed(n: int = 200000, k: int = 1000, nrhs: int = 16, tol: float = 1e-10, reps: int = 2) -> dict:
+    """n = 2e5, k = 1000, cond(A) ~ 1e6, 16 RHS: the FP64 factor + solve against the mixed solve
+    (FP32-accumulated trailing updates, FP64 POTRF, FP64 residual refinement to tol)."""
+    import paper_2305_04635_gb300 as bchol
+    from paper_2305_04635_gb300.mixed import solve_mixed
+
+    A = bandgen.band_product(bandgen.l0_band(n, k, 0, "log1e3"), k)
+    dA = bchol.band_from_numpy(A)
+    b0 = _colmajor(bandgen.rhs(n, nrhs, 0))
+    del A
+    h = bchol.Handle()
+    fp64 = []
+    for _ in range(reps + 1):
+        ab, b = dA.clone(), b0.clone()
+        torch.cuda.synchronize()
+        e0, e1 = _ev()
+        e0.record()
+        info = bchol.factor(ab, k, handle=h)
+        bchol.solve(ab, k, b, handle=h)
+        e1.record()
+        torch.cuda.synchronize()
+        fp64.append(e0.elapsed_time(e1))
+    x64 = b
+    del ab
+    hm = bchol.Handle()
+    mixed, res = [], None
+    for _ in range(reps + 1):
+        torch.cuda.synchronize()
+        e0, e1 = _ev()
+        e0.record()
+        res = solve_mixed(dA, k, b0, tol=tol, handle=hm)
+        e1.record()
+        torch.cuda.synchronize()
+        mixed.append(e0.elapsed_time(e1))
+    x, minfo, iters, resid, corr = res
+    if int(minfo.item()) != 0 or int(info.item()) != 0:
+        raise RuntimeError("mixed leg: factorization failed")
+    diff = float((torch.linalg.norm(x - x64, dim=0) / torch.linalg.norm(x64, dim=0)).max())
+    fp64_ms, mixed_ms = statistics.median(fp64[1:]), statistics.median(mixed[1:])
+    return {"workload": f"n={n}, k={k}, L0 diag log-uniform [1,1e3] (cond ~1e6), {nrhs} RHS",
+            "fp64_factor_solve_ms": round(fp64_ms, 3), "mixed_ms": round(mixed_ms, 3),
+            "speedup_vs_fp64": round(fp64_ms / mixed_ms, 3), "refine_tol_rel_residual": tol,
+            "iterations": iters, "final_rel_residual": resid,
+            "max_rel_diff_x_vs_fp64": diff}
+
+
+def next_adjoint(n: int = 20000, k: int = 200, probe_cols: int = 256, reps: int = 3) -> dict:
+    """n = 2e4, k = 200, loss = 0.5 ||A^{-1} b||^2 + log det A: forward (factor, solve, log det) and the
+    hand-written backward, against forming the band of A^{-1} from solves with unit vectors (timed on
+    probe_cols columns, scaled to n)."""
+    import paper_2305_04635_gb300 as bchol
+    from paper_2305_04635_gb300.autograd import backward, logdet
+
+    A = bandgen.band_product(bandgen.l0_band(n, k, 0, "log1e3", exact=False), k)
+    dA = bchol.band_from_numpy(A)
+    b0 = torch.from_numpy(bandgen.rhs(n, 1, 0)[:, 0].copy()).cuda()
+    h = bchol.Handle()
+    fw, bw, alt = [], [], []
+    E = torch.zeros(probe_cols, n, dtype=torch.float64, device="cuda").T
+    for _ in range(reps + 1):
+        L, x = dA.clone(), b0.clone()
+        torch.cuda.synchronize()
+        e0, e1, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True), \
+            torch.cuda.Event(enable_timing=True)
+        e0.record()
+        bchol.factor(L, k, handle=h)
+        bchol.solve(L, k, x, handle=h)
+        ld = logdet(L, handle=h)
+        e1.record()
+        abar, bbar = backward(L, k, x, x.clone(), 1.0, handle=h)
+        e2.record()
+        torch.cuda.synchronize()
+        fw.append(e0.elapsed_time(e1))
+        bw.append(e1.elapsed_time(e2))
+        E.zero_()
+        E[torch.arange(probe_cols, device="cuda") * (n // probe_cols), torch.arange(probe_cols, device="cuda")] = 1.0
+        torch.cuda.synchronize()
+        e0, e1 = _ev()
+        e0.record()
+        bchol.solve(L, k, E, handle=h)
+        e1.record()
+        torch.cuda.synchronize()
+        alt.append(e0.elapsed_time(e1))
+    if not bool(torch.isfinite(abar).all()) or not bool(torch.isfinite(ld)):
+        raise RuntimeError("adjoint leg: non-finite gradient")
+    fw_ms, bw_ms = statistics.median(fw[1:]), statistics.median(bw[1:])
+    alt_ms = statistics.median(alt[1:]) * n / probe_cols
+    return {"workload": f"n={n}, k={k}, loss = 0.5||A^-1 b||^2 + log det A, b ~ N(0,1)",
+            "forward_ms": round(fw_ms, 3), "backward_ms": round(bw_ms, 3),
+            "backward_over_forward": round(bw_ms / fw_ms, 3),
+            "alt_inverse_columns_by_solves_ms": round(alt_ms, 3),
+            "alt_sample": f"{probe_cols} unit-vector solves, scaled by n/{probe_cols}",
+            "speedup_vs_alt": round(alt_ms / bw_ms, 2)}
+
+
 def cpu_baseline(n: int, ks: list[int], data=None, budget_s: float = 20.0) -> dict:
     """The oracle as it stands on a leading block of each matrix (serial, one core)."""
     import oracle
@@ -310,6 +499,7 @@ def main():
     ap.add_argument("--ks", type=lambda s: [int(x) for x in s.split(",")], default=KS)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-next", action="store_true", help="skip the batched, mixed and adjoint legs")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -341,6 +531,8 @@ def main():
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
     out, data = run_ours(args, rank, world, local)
+    if not args.no_next:
+        out["next"] = {"batched": next_batched(), "mixed": next_mixed(), "adjoint": next_adjoint()}
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args.n, args.ks, budget_s=args.cpu_budget)

@@ -41,12 +41,13 @@ struct bchol_handle_s {
 using namespace bchol;
 
 // Automatic tile size and CTAs per SM, from the n = 1e5 sweep on GB300:
-// b = 16 wins while the factorization is bound by its step chain (k <= 256);
-// b = 32 wins above.  One CTA per SM keeps the chain's tile operations at the
-// full FP64 rate of an SM (k < 1536); two per SM hide task overheads once
-// the trailing update dominates.
-static int auto_tile(int k) { return k <= 256 ? 16 : 32; }
-static int auto_ctas_per_sm(int k) { return k < 1536 ? 1 : 2; }
+// b = 16 wins while the factorization is bound by its diagonal chain (whose
+// step time grows with b^3 on one SM) up to k of about 640; b = 32 wins above,
+// where the trailing updates dominate.  One CTA per SM while the ticket work
+// is small (k <= 256); two per SM above, to overlap the tasks' load and flag
+// latencies.
+static int auto_tile(int k) { return k <= 640 ? 16 : 32; }
+static int auto_ctas_per_sm(int k) { return k <= 256 ? 1 : 2; }
 
 static size_t call_bytes(bchol_handle_t h, int n, int k) {
   const int kk = (n > 0 && k > n - 1) ? n - 1 : k;
@@ -172,7 +173,7 @@ bchol_status_t bchol_plan_task(int n, int k, int tile, long long ticket, int* ty
   if (n < 0 || k < 0 || !(tile == 16 || tile == 32 || tile == 64) || !type || !s || !I || !J) return BCHOL_ERR_ARG;
   const FactorPlan P = make_factor_plan(n, k, tile);
   if (ticket < 0 || (unsigned long long)ticket >= P.total) return BCHOL_ERR_ARG;
-  decode_task(Schedule{P.S, P.p, P.Sreg, P.Treg}, ticket, *type, *s, *I, *J);
+  plan_task(P, ticket, *type, *s, *I, *J);
   return BCHOL_OK;
 }
 

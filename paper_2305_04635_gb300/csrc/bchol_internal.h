@@ -16,12 +16,16 @@ struct FactorPlan {
   int n = 0, k = 0, b = 32, S = 0, p = 0;
   long long Sreg = 0;          // leading ticket blocks of full size (see schedule.cuh)
   long long Treg = 0;          // tasks per such block: 2p + 1 + p(p-1)/2
+  long long Treg_cp = 0;       // tickets per such block with the diagonal chain: 2(p-1) + p(p-1)/2
+  unsigned long long total_cp = 0;  // tickets with the diagonal chain (tiles of 16 and 32)
   unsigned long long total = 0;  // tasks of the whole factorization
   size_t flag_count = 0;       // ints of ready flags: S*(p+1)
   bool f32_update = false;     // mixed precision: trailing updates accumulated in FP32
 };
 
 FactorPlan make_factor_plan(int n, int k, int b);
+// Task t (0-based) of the combined order that one factorization runs.
+void plan_task(const FactorPlan& P, long long t, int& type, int& s, int& I, int& J);
 
 // Device workspace needed by one factorization (control block + flags).
 size_t factor_workspace_bytes(const FactorPlan& plan);

@@ -22,15 +22,30 @@
 // done; it reaches J - s0(I) + 1 when the tile is final (POTRF or TRSM done).
 // A task waits only for tasks with smaller tickets, which are running or
 // finished, so the walk cannot deadlock; every wait is bounded in time.
+//
+// With tiles of 16 or 32 the first CTA of the launch runs the diagonal chain
+// instead (diag_chain.cuh): every task of the diagonal and the first
+// sub-diagonal, fused per step, and the other CTAs take the rest by ticket in
+// the order of decode_cp_ticket.  All CTAs of the launch are resident at once
+// (the grid is sized from the occupancy), and every task the chain waits for
+// precedes, in the combined order, every ticket that waits for the chain, so
+// this walk cannot deadlock either.
+#include <algorithm>
 #include <cstdio>
 
-#include "factor_tasks.cuh"
+#include "diag_chain.cuh"
 
 namespace bchol {
 
-template <int B, bool F32>
+template <int B, bool F32, bool CP>
 __global__ void __launch_bounds__(kThreads, 2) factor_kernel(FactorArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if constexpr (CP) {
+    if (blockIdx.x == 0) {
+      diag_chain<B, F32>(a, *reinterpret_cast<DiagSmem<B, F32>*>(smem_raw));
+      return;
+    }
+  }
   Smem<B>& sm = *reinterpret_cast<Smem<B>*>(smem_raw);
   __shared__ long long s_task;
   __shared__ int s_flag;
@@ -43,7 +58,10 @@ __global__ void __launch_bounds__(kThreads, 2) factor_kernel(FactorArgs a) {
     if (t >= (long long)a.total) break;
     if (threadIdx.x == 0) next = atomicAdd(&a.ctl->ticket, 1ULL);  // claim the next task early
     int type, s, I, J;
-    decode_task(Schedule{a.S, a.p, a.Sreg, a.Treg}, t, type, s, I, J);
+    if constexpr (CP)
+      decode_cp_ticket(Schedule{a.S, a.p, a.Sreg, a.Treg}, t, type, s, I, J);
+    else
+      decode_task(Schedule{a.S, a.p, a.Sreg, a.Treg}, t, type, s, I, J);
     bool ok;
     if (type == kPotrf)
       ok = task_potrf<B>(a, s, sm, &s_flag);
@@ -76,25 +94,34 @@ FactorPlan make_factor_plan(int n, int k, int b) {
   for (int s = (int)P.Sreg; s < P.S; ++s) total += (unsigned long long)sched_block_size(sc, s);
   P.total = total;
   P.flag_count = (size_t)P.S * (size_t)(P.p + 1);
+  P.Treg_cp = cp_treg(P.p);
+  const Schedule cs{P.S, P.p, P.Sreg, P.Treg_cp};
+  unsigned long long tickets = (unsigned long long)cp_panel0(cs);
+  tickets += (unsigned long long)P.Sreg * (unsigned long long)P.Treg_cp;
+  for (int s = (int)P.Sreg; s < P.S; ++s) tickets += (unsigned long long)cp_block_size(cs, s);
+  P.total_cp = tickets;
   return P;
 }
 
 size_t factor_workspace_bytes(const FactorPlan& P) { return 256 + P.flag_count * sizeof(int); }
 
-template <int B, bool F32>
+template <int B, bool F32, bool CP>
 static cudaError_t launch_b(const FactorArgs& a, int ctas_per_sm, cudaStream_t stream) {
-  const size_t smem = sizeof(Smem<B>);
+  size_t smem = sizeof(Smem<B>);
+  if constexpr (CP) smem = std::max(smem, sizeof(DiagSmem<B, F32>));
   cudaError_t e =
-      cudaFuncSetAttribute(factor_kernel<B, F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(factor_kernel<B, F32, CP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, factor_kernel<B, F32>, kThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, factor_kernel<B, F32, CP>, kThreads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
   long long grid = (long long)per_sm * num_sms();
-  if ((unsigned long long)grid > a.total) grid = (long long)a.total;
-  factor_kernel<B, F32><<<(unsigned)grid, kThreads, smem, stream>>>(a);
+  const unsigned long long need = a.total + (CP ? 1 : 0);  // tickets (+ the chain CTA)
+  if ((unsigned long long)grid > need) grid = (long long)need;
+  if (grid < 1) grid = 1;
+  factor_kernel<B, F32, CP><<<(unsigned)grid, kThreads, smem, stream>>>(a);
   return cudaGetLastError();
 }
 
@@ -122,20 +149,77 @@ cudaError_t launch_factor(const FactorPlan& P, double* ab, long long ldab, int* 
   a.stall = -1;
   if (stall_I >= 0 && stall_J >= 0 && stall_I < P.S && stall_J <= stall_I && stall_I - stall_J <= P.p)
     a.stall = stall_J * (P.p + 1) + (stall_I - stall_J);
+  if (P.b <= 32) {  // diagonal chain + tickets
+    a.Treg = P.Treg_cp;
+    a.total = P.total_cp;
+  }
   if (P.f32_update) {
     switch (P.b) {
-      case 16: return launch_b<16, true>(a, ctas_per_sm, stream);
-      case 32: return launch_b<32, true>(a, ctas_per_sm, stream);
-      case 64: return launch_b<64, true>(a, ctas_per_sm, stream);
+      case 16: return launch_b<16, true, true>(a, ctas_per_sm, stream);
+      case 32: return launch_b<32, true, true>(a, ctas_per_sm, stream);
+      case 64: return launch_b<64, true, false>(a, ctas_per_sm, stream);
       default: return cudaErrorInvalidValue;
     }
   }
   switch (P.b) {
-    case 16: return launch_b<16, false>(a, ctas_per_sm, stream);
-    case 32: return launch_b<32, false>(a, ctas_per_sm, stream);
-    case 64: return launch_b<64, false>(a, ctas_per_sm, stream);
+    case 16: return launch_b<16, false, true>(a, ctas_per_sm, stream);
+    case 32: return launch_b<32, false, true>(a, ctas_per_sm, stream);
+    case 64: return launch_b<64, false, false>(a, ctas_per_sm, stream);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// The combined task order of one factorization (host side): for tiles of 16
+// and 32, the diagonal chain's tasks at their places among the tickets;
+// for 64, the ticket order itself.
+void plan_task(const FactorPlan& P, long long t, int& type, int& s, int& I, int& J) {
+  if (P.b > 32) {
+    decode_task(Schedule{P.S, P.p, P.Sreg, P.Treg}, t, type, s, I, J);
+    return;
+  }
+  const Schedule cs{P.S, P.p, P.Sreg, P.Treg_cp};
+  const long long nd = P.p >= 1 ? 3 : 1;
+  auto diag = [&](int st, long long r) {
+    if (st == 0 || P.p == 0 || r == 2) {
+      type = kPotrf;
+      s = I = J = st;
+    } else if (r == 0) {
+      type = kTrsm;
+      s = J = st - 1;
+      I = st;
+    } else {
+      type = kUpd;
+      s = st - 1;
+      I = J = st;
+    }
+  };
+  if (t == 0) {
+    diag(0, 0);
+    return;
+  }
+  t -= 1;
+  long long base = cp_panel0(cs);
+  if (t < base) {
+    decode_cp_ticket(cs, t, type, s, I, J);
+    return;
+  }
+  t -= base;
+  for (int st = 0; st + 1 < P.S; ++st) {
+    if (t < nd) {
+      diag(st + 1, t);
+      return;
+    }
+    t -= nd;
+    const long long bs = cp_block_size(cs, st);
+    if (t < bs) {
+      decode_cp_ticket(cs, base + t, type, s, I, J);
+      return;
+    }
+    t -= bs;
+    base += bs;
+  }
+  type = -1;
+  s = I = J = -1;
 }
 
 }  // namespace bchol

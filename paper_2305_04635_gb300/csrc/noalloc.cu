@@ -54,8 +54,8 @@ static cudaError_t noalloc_scratch(void** out) {
 }
 
 // Tile size and CTAs per SM for half-bandwidth k; the same rule bchol_factor uses by default.
-static int noalloc_tile(int k) { return k <= 256 ? 16 : 32; }
-static int noalloc_ctas_per_sm(int k) { return k < 1536 ? 1 : 2; }
+static int noalloc_tile(int k) { return k <= 640 ? 16 : 32; }
+static int noalloc_ctas_per_sm(int k) { return k <= 256 ? 1 : 2; }
 
 }  // namespace bchol
 

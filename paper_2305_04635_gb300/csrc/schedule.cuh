@@ -98,4 +98,95 @@ __host__ __device__ inline void decode_task(const Schedule& a, long long t, int&
   }
 }
 
+// ----------------------------------------------------------------------------
+// Order of the single-matrix kernel with a diagonal chain.  One CTA runs every
+// task of the diagonal and the first sub-diagonal, in the fused form
+//     DIAG(s) = TRSM(s, s-1), UPD(s, s, s-1), POTRF(s)   (only POTRF(s) when s = 0 or p = 0)
+// so that the critical path of Algorithm 1 (POTRF(s) -> TRSM(s+1,s) ->
+// DSYRK(s+1,s+1) -> POTRF(s+1)) never leaves one SM.  The other CTAs take the
+// remaining tasks by ticket: first panel'(0), then for s = 0, 1, ...
+//     near'(s)    UPD(s+1+r, s+1, s),  r = 1..m_s-1
+//     panel'(s+1) TRSM(s+2+r, s+1),    r = 1..m_{s+1}-1
+//     far(s)      UPD(I, J, s), J = s+2..s+m_s, I = J..s+m_s
+// with panel'(s) = TRSM(s+1+r, s), r = 1..m_s-1.  In the combined order
+//     DIAG(0), panel'(0), DIAG(1), block'(0), DIAG(2), block'(1), ...
+// every task comes after the tasks it reads; DIAG(s+1) reads only tiles
+// finished in blocks up to s-1, and the tickets of block s read DIAG(s+1) at
+// most.  Regular blocks (m_s = m_{s+1} = p) hold 2(p-1) + p(p-1)/2 tickets.
+
+__host__ __device__ inline long long cp_treg(int p) { return p >= 1 ? 2LL * (p - 1) + (long long)p * (p - 1) / 2 : 0; }
+
+__host__ __device__ inline long long cp_panel0(const Schedule& a) {
+  const int m0 = sched_m(a, 0);
+  return m0 > 1 ? m0 - 1 : 0;
+}
+
+__host__ __device__ inline long long cp_block_size(const Schedule& a, int s) {
+  const long long ms = sched_m(a, s);
+  long long size = (ms > 1 ? ms - 1 : 0) + ms * (ms - 1) / 2;
+  if (s + 1 < a.S) {
+    const long long m1 = sched_m(a, s + 1);
+    size += m1 > 1 ? m1 - 1 : 0;
+  }
+  return size;
+}
+
+// Ticket t (0-based, tickets only) -> task.  `a.Treg` must be cp_treg(p).
+__host__ __device__ inline void decode_cp_ticket(const Schedule& a, long long t, int& type, int& s, int& I, int& J) {
+  const long long P0 = cp_panel0(a);
+  if (t < P0) {  // panel'(0)
+    type = kTrsm;
+    s = 0;
+    J = 0;
+    I = 2 + (int)t;
+    return;
+  }
+  t -= P0;
+  if (a.Treg > 0 && t < a.Sreg * a.Treg) {
+    s = (int)(t / a.Treg);
+    t -= (long long)s * a.Treg;
+  } else {
+    t -= a.Sreg * a.Treg;
+    s = (int)a.Sreg;
+    while (true) {
+      const long long size = cp_block_size(a, s);
+      if (t < size) break;
+      t -= size;
+      ++s;
+    }
+  }
+  const int ms = sched_m(a, s);
+  const long long nnear = ms > 1 ? ms - 1 : 0;
+  if (t < nnear) {  // near'(s)
+    type = kUpd;
+    J = s + 1;
+    I = s + 2 + (int)t;
+    return;
+  }
+  t -= nnear;
+  if (s + 1 < a.S) {  // panel'(s+1)
+    const int m1 = sched_m(a, s + 1);
+    const long long npan = m1 > 1 ? m1 - 1 : 0;
+    if (t < npan) {
+      type = kTrsm;
+      s = s + 1;
+      J = s;
+      I = s + 2 + (int)t;
+      return;
+    }
+    t -= npan;
+  }
+  type = kUpd;  // far(s)
+  J = s + 2;
+  while (true) {
+    const long long cnt = s + ms - J + 1;
+    if (t < cnt) {
+      I = J + (int)t;
+      return;
+    }
+    t -= cnt;
+    ++J;
+  }
+}
+
 }  // namespace bchol
