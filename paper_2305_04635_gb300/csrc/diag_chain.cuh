@@ -59,10 +59,12 @@ struct DiagSmem {
   double L[B * B];     // L(s, s), kept for the next step's TRSM
   float Xf[F32 ? B * B : 1];
   float Lf[F32 ? B * B : 1];
-  double r[B];    // 1 / L(j, j): the reciprocal square roots of the last POTRF's pivots
   float rf[F32 ? B : 1];
-  double lj[B];   // L(j, j)
-  double col[B];  // column j of L while POTRF runs
+  double d[B];    // pivots d_j of the Schur recurrence
+  double inv[B];  // 1 / d_j
+  double r[B];    // 1 / sqrt(d_j) = 1 / L(j, j)
+  double q[B];    // q_{j+1} = D(j+1, j)^2 after the updates of columns < j
+  double y[B];    // D(i, j) / d_j for the rank-1 update of column j
   unsigned short tri[B * (B + 1) / 2];  // lower-triangle entries (l << 8 | i), last column first
   int in_ready;   // prefetcher: the inputs of steps < in_ready are in place
   int consumed;   // compute: steps < consumed are finished (their buffers are free)
@@ -72,18 +74,40 @@ struct DiagSmem {
   int ok;         // compute: broadcast of a wait result
 };
 
+constexpr unsigned kPollNs = 64;  // back-off of the service warps' polls
+
 // Bounded wait (one thread) until *p >= target in shared memory.
 __device__ __forceinline__ bool wait_smem_geq(const int* p, int target, const int* stop, Control* ctl,
                                               int* status, uint64_t limit_ns) {
   if (ld_acquire_cta(p) >= target) return true;
   const uint64_t t0 = globaltimer_ns();
   while (true) {
+    __nanosleep(kPollNs);  // keep the poll off the compute warps' shared-memory pipe
     if (ld_acquire_cta(p) >= target) return true;
     if (*(volatile const int*)stop) return false;
     if (ld_relaxed(&ctl->abort) != 0) return false;
     if (globaltimer_ns() - t0 > limit_ns) {
       atomicExch(status, kStatusTimeout);
       atomicExch(&ctl->abort, 1);
+      return false;
+    }
+  }
+}
+
+// wait_tile with a back-off between polls (the chain CTA's prefetch warp).
+__device__ __forceinline__ bool wait_tile_poll(const FactorArgs& a, int I, int J, int target) {
+  const int f = fidx(a, I, J);
+  if (f == a.stall) target = 0x7fffffff;
+  const int* flag = &a.flags[f];
+  if (ld_acquire(flag) >= target) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (true) {
+    __nanosleep(kPollNs);
+    if (ld_acquire(flag) >= target) return true;
+    if (ld_relaxed(&a.ctl->abort) != 0) return false;
+    if (globaltimer_ns() - t0 > a.wait_ns) {
+      atomicExch(a.status, kStatusTimeout);
+      atomicExch(&a.ctl->abort, 1);
       return false;
     }
   }
@@ -131,9 +155,10 @@ __device__ void diag_publisher(const FactorArgs& a, DiagSmem<B, F32>& sm, int la
 }
 
 // ----------------------------------------------------------- prefetcher (warp 5)
-// For step s: waits until the other CTAs have applied every update of A(s, s-1)
-// and A(s, s) except the step s-1 DSYRK (steps s0(s) .. s-2), and copies both
-// tiles into buffer s & 1 (free once step s-2 is finished).
+// For step s: waits until the other CTAs have applied every update of A(s, s)
+// and A(s, s-1) except the step s-1 DSYRK (steps s0(s) .. s-2), and copies both
+// tiles into buffer s & 1 (free once step s-2 is finished).  A(s, s) is usually
+// ready first: its last outside update comes a step earlier.
 template <int B, bool F32>
 __device__ void diag_prefetcher(const FactorArgs& a, DiagSmem<B, F32>& sm, int lane) {
   const uint64_t limit = 4 * a.wait_ns;
@@ -144,17 +169,19 @@ __device__ void diag_prefetcher(const FactorArgs& a, DiagSmem<B, F32>& sm, int l
     int ok = 1;
     if (lane == 0) {
       if (s >= 2) ok = wait_smem_geq(&sm.consumed, s - 1, &sm.stop, a.ctl, a.status, limit);
-      if (ok && has_x) ok = wait_tile(a, s, s - 1, s - 1 - s0);
+      if (ok) ok = wait_tile_poll(a, s, s, has_x ? s - 1 - s0 : s - s0);
     }
     ok = __shfl_sync(0xffffffffu, ok, 0);
     __syncwarp();
     if (!ok) break;
-    if (has_x) load_tile_lanes<B>(a, s, s - 1, sm.X[cur], lane);
-    if (lane == 0) ok = wait_tile(a, s, s, has_x ? s - 1 - s0 : s - s0);
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    __syncwarp();
-    if (!ok) break;
     load_tile_lanes<B>(a, s, s, sm.D[cur], lane);
+    if (has_x) {
+      if (lane == 0) ok = wait_tile_poll(a, s, s - 1, s - 1 - s0);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      __syncwarp();
+      if (!ok) break;
+      load_tile_lanes<B>(a, s, s - 1, sm.X[cur], lane);
+    }
     __syncwarp();
     if (lane == 0) st_release_cta(&sm.in_ready, s + 1);
   }
@@ -168,6 +195,8 @@ __device__ void diag_prefetcher(const FactorArgs& a, DiagSmem<B, F32>& sm, int l
 // X := X L^{-T} with L = L(s-1, s-1) and r = 1/diag(L), in place.  Warp w owns
 // rows w*B/4 ..; G lanes share a row, lane g keeps columns g, g+G, ... in
 // registers; column j is finished by its owner and shuffled to the row group.
+// (A product with an explicit L^{-1} would drop the substitution chain, but
+// forming L^{-1} inside POTRF costs the chain CTA more than it saves here.)
 template <int B, typename VT, bool F32>
 __device__ __forceinline__ void diag_trsm(DiagSmem<B, F32>& sm, double* X, int tid) {
   constexpr int RPW = B / 4, G = 32 / RPW, C = B / G;
@@ -205,13 +234,18 @@ __device__ __forceinline__ void diag_trsm(DiagSmem<B, F32>& sm, double* X, int t
 
 // --------------------------------------------------------------------- DSYRK
 // D -= X X^T on the lower triangle (FP32 products and sums in the mixed form).
+// 128 threads: full passes of one entry per thread, then the R left-over
+// entries split by terms over 128/R lanes each and summed by shuffles, so the
+// four sub-partitions get the same number of FP64 instructions.
 template <int B, typename VT, bool F32>
 __device__ __forceinline__ void diag_syrk(DiagSmem<B, F32>& sm, const double* X, double* D, int tid) {
-  constexpr int NT = B * (B + 1) / 2;
+  constexpr int NT = B * (B + 1) / 2, PASSES = NT / 128, R = NT - 128 * PASSES;
+  constexpr int TPE = 128 / R, TERMS = B / TPE;
+  static_assert(R > 0 && 128 % R == 0 && B % TPE == 0 && TPE <= 32, "DSYRK split");
   const VT* Xm;
   if constexpr (F32) Xm = sm.Xf; else Xm = X;
-  for (int e = tid; e < NT; e += 128) {
-    const int code = sm.tri[e];
+  for (int ps = 0; ps < PASSES; ++ps) {
+    const int code = sm.tri[tid + 128 * ps];
     const int i = code & 0xff, l = code >> 8;
     if constexpr (F32) {
       float acc = 0.0f;
@@ -225,40 +259,53 @@ __device__ __forceinline__ void diag_syrk(DiagSmem<B, F32>& sm, const double* X,
       D[l * B + i] = acc;
     }
   }
+  const int code = sm.tri[128 * PASSES + tid / TPE], part = tid % TPE;
+  const int i = code & 0xff, l = code >> 8;
+  VT acc = 0;
+#pragma unroll
+  for (int m = part * TERMS; m < (part + 1) * TERMS; ++m) {
+    if constexpr (F32) acc = fmaf(Xm[m * B + i], Xm[m * B + l], acc);
+    else acc = fma(Xm[m * B + i], Xm[m * B + l], acc);
+  }
+#pragma unroll
+  for (int off = TPE / 2; off >= 1; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (part == 0) D[l * B + i] -= (double)acc;
 }
 
 // -------------------------------------------------------------------- POTRF
-// Right-looking Cholesky of D (jmax valid columns) into sm.L.  Warp 0 lane 0
-// runs the pivot recurrence  x = D(j+1,j) r_j,  d_{j+1} = D(j+1,j+1) - x^2,
-// r_{j+1} = rsqrt(d_{j+1}); warps 1-3 then form column j of L and apply its
-// rank-1 update to the trailing triangle (all but D(j+1,j+1), which the
-// recurrence owns).  Warp 0 needs column j-1's updates before pivot j+1, so
-// the updates run one column behind the recurrence.
+// Cholesky of D (jmax valid columns) by the Schur recurrence without square
+// roots on the chain: with d_j the j-th pivot and y = D(:, j) / d_j,
+//     D(i, l) -= y_i D(l, j)   (j < l <= i),   d_{j+1} = D(j+1, j+1) - D(j+1, j)^2 / d_j,
+// and L(i, j) = D(i, j) r_j with r_j = 1/sqrt(d_j) afterwards (all square
+// roots in one batch once the chain is done).  Warp 0 lane 0 runs only the
+// pivot recurrence (one DFMA and one division per column), alone on its
+// sub-partition; warps 1-3 form y and apply the rank-1 update one column
+// behind (two entries per thread at a time, so their loads and FMAs overlap).
+// D(j+1, j+1) and q_{j+1} = D(j+1, j)^2 reach the recurrence through shared
+// memory; the recurrence's own entry D(j+1, j+1) is left out of column j's update.
 template <int B, bool F32>
 __device__ __forceinline__ void diag_potrf(DiagSmem<B, F32>& sm, double* D, int jmax, int tid) {
   const int warp = tid >> 5, lane = tid & 31;
   if (warp == 0) {
-    double r = 0.0;
+    double inv = 0.0;
     if (lane == 0) {
       const double d = D[0];
+      if (jmax >= 2) sm.q[1] = D[1] * D[1];
       if (!(d > 0.0)) sm.fail = 1;
-      r = rsqrt(d);
-      sm.r[0] = r;
-      sm.lj[0] = d * r;
+      sm.d[0] = d;
+      inv = 1.0 / d;
+      sm.inv[0] = inv;
     }
-    __syncwarp();
     bar_arrive(kBarP, 128);
     for (int j = 0; j + 1 < jmax; ++j) {
       if (j >= 1) bar_sync(kBarU + ((j - 1) & 1), 128);
       if (lane == 0) {
-        const double x = D[j * B + j + 1] * r;
-        const double v = fma(-x, x, D[(j + 1) * B + j + 1]);
-        if (!(v > 0.0) && sm.fail == 0) sm.fail = j + 2;
-        r = rsqrt(v);
-        sm.r[j + 1] = r;
-        sm.lj[j + 1] = v * r;
+        const double d = fma(-sm.q[j + 1], inv, D[(j + 1) * B + j + 1]);
+        if (!(d > 0.0) && sm.fail == 0) sm.fail = j + 2;
+        sm.d[j + 1] = d;
+        inv = 1.0 / d;
+        sm.inv[j + 1] = inv;
       }
-      __syncwarp();
       bar_arrive(kBarP + ((j + 1) & 1), 128);
     }
     if (jmax >= 2) bar_sync(kBarU + ((jmax - 2) & 1), 128);
@@ -266,23 +313,30 @@ __device__ __forceinline__ void diag_potrf(DiagSmem<B, F32>& sm, double* D, int 
     const int u = tid - 32;
     for (int j = 0; j < jmax; ++j) {
       bar_sync(kBarP + (j & 1), 128);
-      const double r = sm.r[j];
-      for (int i = j + 1 + u; i < jmax; i += 96) {
-        const double lc = D[j * B + i] * r;
-        sm.col[i] = lc;
-        sm.L[j * B + i] = lc;
-      }
-      if (u == 0) sm.L[j * B + j] = sm.lj[j];
       if (j + 1 < jmax) {
-        __syncwarp();
+        const double inv = sm.inv[j];
+        for (int i = j + 1 + u; i < jmax; i += 96) sm.y[i] = D[j * B + i] * inv;
         bar_sync(kBarW, 96);
         const int T = (B - 1 - j) * (B - j) / 2;
-        for (int e = u; e < T; e += 96) {
-          const int code = sm.tri[e];
-          const int i = code & 0xff, l = code >> 8;
-          if (i < jmax && !(i == j + 1 && l == j + 1)) D[l * B + i] = fma(-sm.col[i], sm.col[l], D[l * B + i]);
+        for (int e = u; e < T; e += 192) {
+          const int e2 = e + 96;
+          const int c1 = sm.tri[e], c2 = e2 < T ? (int)sm.tri[e2] : 0;
+          const int i1 = c1 & 0xff, l1 = c1 >> 8, i2 = c2 & 0xff, l2 = c2 >> 8;
+          const bool ok1 = i1 < jmax && !(i1 == j + 1 && l1 == j + 1);
+          const bool ok2 = e2 < T && i2 < jmax && !(i2 == j + 1 && l2 == j + 1);
+          const double a1 = D[l1 * B + i1], x1 = D[j * B + l1], y1 = sm.y[i1];
+          const double a2 = D[l2 * B + i2], x2 = D[j * B + l2], y2 = sm.y[i2];
+          const double v1 = fma(-y1, x1, a1);
+          const double v2 = fma(-y2, x2, a2);
+          if (ok1) {
+            D[l1 * B + i1] = v1;
+            if (i1 == j + 2 && l1 == j + 1) sm.q[j + 2] = v1 * v1;
+          }
+          if (ok2) {
+            D[l2 * B + i2] = v2;
+            if (i2 == j + 2 && l2 == j + 1) sm.q[j + 2] = v2 * v2;
+          }
         }
-        __syncwarp();
         bar_arrive(kBarU + (j & 1), 128);
       }
     }
@@ -309,8 +363,8 @@ __device__ void diag_compute(const FactorArgs& a, DiagSmem<B, F32>& sm, int tid)
       bar_sync(kBarC, 128);
       if (tid == 0) st_release_cta(&sm.pub, ++pub);
       diag_syrk<B, VT, F32>(sm, X, D, tid);
-      bar_sync(kBarC, 128);
     }
+    bar_sync(kBarC, 128);
     const int jmax = min(B, a.n - s * B);
     diag_potrf<B, F32>(sm, D, jmax, tid);
     bar_sync(kBarC, 128);
@@ -322,10 +376,23 @@ __device__ void diag_compute(const FactorArgs& a, DiagSmem<B, F32>& sm, int tid)
       }
       return;
     }
-    store_tile_compute<B>(a, s, s, sm.L, tid);
+    if (tid < jmax) sm.r[tid] = rsqrt(sm.d[tid]);
+    bar_sync(kBarC, 128);
     if constexpr (F32) {
-      for (int idx = tid; idx < B * B; idx += 128) sm.Lf[idx] = (float)sm.L[idx];
       if (tid < B) sm.rf[tid] = (float)sm.r[tid];
+    }
+    // L(i, j) = D(i, j) r_j and L(j, j) = d_j r_j: into shared memory for the
+    // next step's TRSM and into the band
+    for (int idx = tid; idx < B * B; idx += 128) {
+      const int i = idx % B, j = idx / B;
+      if (i >= j && i < jmax) {
+        const double rj = sm.r[j];
+        const double lv = (i == j) ? sm.d[j] * rj : D[idx] * rj;
+        sm.L[idx] = lv;
+        if constexpr (F32) sm.Lf[idx] = (float)lv;
+        const int gi = s * B + i, gj = s * B + j, dd = gi - gj;
+        if (dd <= a.k) a.ab[dd + (long long)gj * a.ldab] = lv;
+      }
     }
     bar_sync(kBarC, 128);
     if (tid == 0) {
