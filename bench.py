@@ -289,6 +289,7 @@ def next_batched(count: int = 512, reps: int = 3) -> dict:
     F = sum(flops_eq1(n, k) for n, k in zip(ns, ks))
 
     def restore():
+        torch.cuda.synchronize()          # nothing may still be writing the work copies
         for w, p in zip(work, pr):
             w.copy_(p)
         for w, p in zip(bw, bpr):

@@ -28,7 +28,7 @@ namespace bchol {
 
 constexpr int kSB = 32;        // solve block
 constexpr int kNRC = 8;        // right-hand sides per pass, FP64 sweeps
-constexpr int kNRC32 = 16;     // right-hand sides per pass, FP32 sweeps
+constexpr int kNRC32 = 8;      // right-hand sides per pass, FP32 sweeps
 constexpr int kSThreads = 256;
 constexpr int kSWarps = kSThreads / 32;
 constexpr int kQ = kSB / kSWarps;   // columns per warp in a 32 x 32 product
