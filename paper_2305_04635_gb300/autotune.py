@@ -61,10 +61,13 @@ def tune_batch(bands, ks, rhs=None, candidates=CANDIDATES, reps: int = 1, cache_
                 for r, r0 in zip(rs, rhs):
                     if r is not None:
                         r.copy_(r0)
+            # time on the stream the batch runs on (the handle's own, if it has one)
+            stream = h._stream if h._stream is not None else torch.cuda.current_stream()
+            torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
+            e0.record(stream)
             batch.run(h)
-            e1.record()
+            e1.record(stream)
             torch.cuda.synchronize()
             if rep > 0:
                 times.append(e0.elapsed_time(e1))

@@ -109,11 +109,11 @@ __global__ void __launch_bounds__(kThreads, 2) factor_batched_kernel(BatchArgs g
         unsigned long long t = 0;
         if (rd * 32 + lane < g.count) {
           Control* c = g.ctl + mm;
-          if (ld_relaxed(&c->pad) == 0) {
+          if (ld_relaxed(&c->retired) == 0) {
             t = ld_relaxed_u64(&c->ticket);
             const FactorArgs a = matrix_args(g, mm);
             if (t >= a.total || ld_relaxed(&c->abort) != 0) {
-              if (atomicCAS(&c->pad, 0, 1) == 0) atomicAdd(g.retired, 1);
+              if (atomicCAS(&c->retired, 0, 1) == 0) atomicAdd(g.retired, 1);
             } else {
               int type, s, I, J;
               decode_task(Schedule{a.S, a.p, a.Sreg, a.Treg}, (long long)t, type, s, I, J);

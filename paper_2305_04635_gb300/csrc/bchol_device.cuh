@@ -38,8 +38,16 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 struct Control {
   unsigned long long ticket;  // next task ticket
   int abort;                  // != 0: stop (a pivot failed or a wait ran out)
+  int chain_sm;               // 1 + the SM of the diagonal-chain CTA, 0 until it is known
+  int retired;                // batched launch: every ticket of this matrix is taken
   int pad;
 };
+
+__device__ __forceinline__ int sm_id() {
+  int v;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(v));
+  return v;
+}
 
 // Spin (one thread) until *flag >= target.  Returns false when the launch is
 // aborted or the wait exceeds wait_ns; a timeout is recorded in *status and

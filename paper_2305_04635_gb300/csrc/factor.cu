@@ -40,15 +40,28 @@ namespace bchol {
 template <int B, bool F32, bool CP>
 __global__ void __launch_bounds__(kThreads, 2) factor_kernel(FactorArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ long long s_task;
+  __shared__ int s_flag;
   if constexpr (CP) {
     if (blockIdx.x == 0) {
+      if (threadIdx.x == 0) st_release(&a.ctl->chain_sm, sm_id() + 1);
       diag_chain<B, F32>(a, *reinterpret_cast<DiagSmem<B, F32>*>(smem_raw));
       return;
     }
+    // A ticket CTA on the chain CTA's SM leaves: the chain's FP64 work is the
+    // critical path and each SM sub-partition's FP64 unit is shared.  (All CTAs
+    // are resident at once, so the chain CTA publishes its SM promptly; the
+    // wait is bounded and a CTA that gives up simply stays.)
+    if (threadIdx.x == 0) {
+      int c = ld_acquire(&a.ctl->chain_sm);
+      const uint64_t t0 = globaltimer_ns();
+      while (c == 0 && globaltimer_ns() - t0 < 200000ull) c = ld_acquire(&a.ctl->chain_sm);
+      s_flag = (c == sm_id() + 1);
+    }
+    __syncthreads();
+    if (s_flag) return;
   }
   Smem<B>& sm = *reinterpret_cast<Smem<B>*>(smem_raw);
-  __shared__ long long s_task;
-  __shared__ int s_flag;
   unsigned long long next = 0;
   if (threadIdx.x == 0) next = atomicAdd(&a.ctl->ticket, 1ULL);
   while (true) {
