@@ -2,8 +2,9 @@
 //
 // A copy of A is equilibrated, Ã = S A S with S = diag(A)^{-1/2}, and factored
 // with the tile algorithm of the paper (Algorithm 1) in which the trailing
-// SYRK/GEMM updates accumulate in FP32 (POTRF and TRSM stay FP64).  The
-// solution is then refined in FP64:
+// SYRK/GEMM updates accumulate in FP32 and the panel TRSMs run in FP32 (the
+// diagonal POTRF stays FP64; the factor is stored in FP64).  The solution is
+// then refined in FP64:
 //     x_0 = S Ã^{-1} S b,     r_i = b - A x_i  (FP64),
 //     d_i = S Ã^{-1} S r_i    (the correction solve, FP32 arithmetic),
 //     x_{i+1} = x_i + d_i     (FP64),

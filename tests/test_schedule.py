@@ -53,3 +53,51 @@ def test_task_count_matches_closed_form():
         p = math.ceil(k / b)
         total = (S - p) * (1 + p * (p + 3) // 2) + sum(1 + m * (m + 3) // 2 for m in range(p))
         assert bchol.load_library().bchol_plan_task_count(n, k, b) == total
+
+
+def _deps(task, p):
+    typ, s, I, J = task
+    if typ == 0:
+        return [(2, s - 1, s, s)] if s >= 1 and s - 1 >= max(0, s - p) else []
+    if typ == 1:
+        return [(0, s, s, s)] + ([(2, s - 1, I, s)] if s - 1 >= max(0, I - p) else [])
+    return [(1, s, I, s), (1, s, J, s)] + ([(2, s - 1, I, J)] if s - 1 >= max(0, I - p) else [])
+
+
+def _is_chain(task):
+    """Tasks the diagonal-chain CTA runs (tiles of 16 and 32): POTRF(s), TRSM(s, s-1), UPD(s, s, s-1)."""
+    typ, s, I, J = task
+    return typ == 0 or (typ == 1 and I == s + 1) or (typ == 2 and I == J == s + 1)
+
+
+@pytest.mark.parametrize("workers", [1, 2, 5])
+@pytest.mark.parametrize("n,k,b", [(1000, 50, 16), (640, 200, 32), (777, 90, 16), (300, 16, 16), (100, 0, 16),
+                                   (129, 64, 64)])
+def test_launch_cannot_deadlock(n, k, b, workers):
+    """Simulate the persistent launch: the chain CTA runs its tasks in order; each ticket CTA claims
+    the next ticket, and claims one more before it starts the one it holds (as the kernel does).
+    A task runs once every task it reads is done.  Progress must never stop."""
+    order = bchol.plan_tasks(n, k, b)
+    kk = min(k, n - 1)
+    S = math.ceil(n / b)
+    p = min(math.ceil(kk / b), S - 1)
+    chain_mode = b <= 32
+    chain = [t for t in order if chain_mode and _is_chain(t)]
+    tickets = [t for t in order if not (chain_mode and _is_chain(t))]
+    done = set()
+    ci, next_ticket = 0, 0
+    held = [[] for _ in range(workers)]
+    while len(done) < len(order):
+        progress = False
+        for w in range(workers):
+            while len(held[w]) < 2 and next_ticket < len(tickets):
+                held[w].append(tickets[next_ticket])
+                next_ticket += 1
+            if held[w] and all(d in done for d in _deps(held[w][0], p)):
+                done.add(held[w].pop(0))
+                progress = True
+        if ci < len(chain) and all(d in done for d in _deps(chain[ci], p)):
+            done.add(chain[ci])
+            ci += 1
+            progress = True
+        assert progress, f"stalled with {len(done)} of {len(order)} tasks done"
