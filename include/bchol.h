@@ -244,6 +244,15 @@ bchol_status_t bchol_set_stall_tile(bchol_handle_t handle, int I, int J);
 long long bchol_plan_task_count(int n, int k, int tile);
 bchol_status_t bchol_plan_task(int n, int k, int tile, long long ticket, int* type, int* s, int* I, int* J);
 
+/* Self-check of the reciprocal the diagonal POTRF's pivot recurrence uses
+ * (d_{j+1} = A(j+1,j+1) - A(j+1,j)^2 / d_j, the Schur complement of Sec. 3's
+ * POTRF step): y[i] = 1/x[i] by that routine, for n device doubles x (n >= 0;
+ * x and y device pointers, caller-owned, may not overlap).  Asynchronous on
+ * the handle's stream.  For positive normal x the relative error is a few
+ * units in the last place; tests compare it with IEEE division.  Returns
+ * BCHOL_ERR_ARG on a null handle or pointer with n > 0. */
+bchol_status_t bchol_check_pivot_rcp(bchol_handle_t handle, const double* x, double* y, int n);
+
 /* Number of factor-kernel and solve-kernel launches made by the last call on
  * this handle (for launch accounting). */
 int bchol_last_launch_count(bchol_handle_t handle);

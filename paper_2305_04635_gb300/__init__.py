@@ -84,6 +84,7 @@ def load_library():
         "bchol_factor_batched": ([P, I, P, P, P, P, P, P, P, P], I),
         "bchol_plan_task_count": ([I, I, I], ctypes.c_longlong),
         "bchol_plan_task": ([I, I, I, ctypes.c_longlong, P, P, P, P], I),
+        "bchol_check_pivot_rcp": ([P, P, P, I], I),
         "bchol_version": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():

@@ -177,6 +177,15 @@ bchol_status_t bchol_plan_task(int n, int k, int tile, long long ticket, int* ty
   return BCHOL_OK;
 }
 
+bchol_status_t bchol_check_pivot_rcp(bchol_handle_t h, const double* x, double* y, int n) {
+  if (!h || n < 0 || (n > 0 && (!x || !y))) return BCHOL_ERR_ARG;
+  if (launch_pivot_rcp(x, y, n, h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return BCHOL_ERR_CUDA;
+  }
+  return BCHOL_OK;
+}
+
 int bchol_last_launch_count(bchol_handle_t h) { return h ? h->last_launches : 0; }
 
 const char* bchol_version(void) { return "bchol 0.1.0 (sm_103a)"; }

@@ -32,6 +32,7 @@ size_t factor_workspace_bytes(const FactorPlan& plan);
 
 // Launch the persistent factor kernel.  `ws` holds factor_workspace_bytes()
 // bytes; `status` is a device int that outlives the call (timeout record).
+cudaError_t launch_pivot_rcp(const double* x, double* y, int n, cudaStream_t stream);
 cudaError_t launch_factor(const FactorPlan& plan, double* ab, long long ldab, int* info, void* ws, int* status,
                           uint64_t wait_ns, int ctas_per_sm, int stall_I, int stall_J, cudaStream_t stream);
 

@@ -2,8 +2,9 @@
 //
 // One CTA of the persistent launch runs, for s = 0, 1, ..., S-1,
 //     DIAG(s) = TRSM(s, s-1), UPD(s, s, s-1) (the DSYRK), POTRF(s)
-// i.e. the whole critical path of Algorithm 1, with L(s-1, s-1) kept in
-// shared memory between steps.  L(s, s-1) is published as soon as it is
+// i.e. the whole critical path of Algorithm 1, with the factor of the
+// previous diagonal tile (as its unit lower part and 1/diag) kept in shared
+// memory between steps.  L(s, s-1) is published as soon as it is
 // solved (the updates UPD(I, s, s-1) of the other CTAs need it), before the
 // DSYRK and the POTRF run.
 //
@@ -13,15 +14,30 @@
 // sub-partition: four compute warps (0-3, one per sub-partition) carry the
 // FP64 work; in POTRF warp 0 runs the pivot recurrence alone on its
 // sub-partition while warps 1-3 apply the rank-1 updates one column behind.
-// Two more warps issue no FP64 at all: warp 4 publishes ready counters (so no
-// compute warp stalls on a release), warp 5 waits for the next step's input
-// tiles and copies them into a second buffer while the current step runs.
+// The other warps issue no FP64 at all: warp 4 publishes ready counters (so
+// no compute warp stalls on a release), warps 5-7 wait for the next step's
+// input tiles and copy them into a second buffer while the current step runs.
 #pragma once
 #include <type_traits>
 
 #include "factor_tasks.cuh"
 
 namespace bchol {
+
+// 1/d for the pivot recurrence: the hardware seed rcp.approx.ftz.f64 (relative
+// error below 2^-20, measured) refined by one step of the cubic Newton-type
+// iteration y1 = y0 (1 + e + e^2), e = 1 - d y0, whose error is e^3 (below
+// 2^-60) plus the rounding of the three FMAs.  Three dependent FP64
+// operations instead of a full division on the chain.  d > 0 in use; other
+// inputs give a non-finite or meaningless result, and the caller has already
+// flagged the pivot.
+__device__ __forceinline__ double pivot_rcp(double d) {
+  double y0;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y0) : "d"(d));
+  const double e = fma(-d, y0, 1.0);
+  const double p = fma(e, e, e);
+  return fma(y0, p, y0);
+}
 
 // Named barriers (whole warps only: the warp is reconverged first).
 __device__ __forceinline__ void bar_sync(int id, int count) {
@@ -50,21 +66,21 @@ constexpr int kBarC = 1;     // compute warps 0-3 (128 threads)
 constexpr int kBarP = 2;     // 2, 3 by parity of j: pivot j is ready (warp 0 arrives, warps 1-3 wait)
 constexpr int kBarU = 4;     // 4, 5 by parity of j: column j's updates are done (warps 1-3 arrive, warp 0 waits)
 constexpr int kBarW = 6;     // update warps 1-3 (96 threads)
-constexpr int kBarInit = 7;  // warps 0-5 (192 threads)
+constexpr int kBarInit = 7;  // the whole CTA (256 threads)
+constexpr int kBarPF = 8;    // prefetch warps 5-7 (96 threads)
 
 template <int B, bool F32>
 struct DiagSmem {
   double X[2][B * B];  // A(s, s-1) in, L(s, s-1) out; buffer s & 1
   double D[2][B * B];  // A(s, s); buffer s & 1
-  double L[B * B];     // L(s, s), kept for the next step's TRSM
+  double U[B * B];     // unit lower factor of L(s, s): U(i, j) = L(i, j) / L(j, j), kept for the next TRSM
   float Xf[F32 ? B * B : 1];
-  float Lf[F32 ? B * B : 1];
+  float Uf[F32 ? B * B : 1];
   float rf[F32 ? B : 1];
   double d[B];    // pivots d_j of the Schur recurrence
   double inv[B];  // 1 / d_j
   double r[B];    // 1 / sqrt(d_j) = 1 / L(j, j)
   double q[B];    // q_{j+1} = D(j+1, j)^2 after the updates of columns < j
-  double y[B];    // D(i, j) / d_j for the rank-1 update of column j
   unsigned short tri[B * (B + 1) / 2];  // lower-triangle entries (l << 8 | i), last column first
   int in_ready;   // prefetcher: the inputs of steps < in_ready are in place
   int consumed;   // compute: steps < consumed are finished (their buffers are free)
@@ -72,6 +88,8 @@ struct DiagSmem {
   int stop;       // any role: stop now
   int fail;       // POTRF: first non-positive pivot (1-based column in the tile), or 0
   int ok;         // compute: broadcast of a wait result
+  int pf_ok_d;    // prefetch: broadcast of the wait for A(s, s)
+  int pf_ok_x;    // prefetch: broadcast of the wait for A(s, s-1)
 };
 
 constexpr unsigned kPollNs = 64;  // back-off of the service warps' polls
@@ -114,9 +132,9 @@ __device__ __forceinline__ bool wait_tile_poll(const FactorArgs& a, int I, int J
 }
 
 template <int B>
-__device__ __forceinline__ void load_tile_lanes(const FactorArgs& a, int I, int J, double* s, int lane) {
-#pragma unroll 8
-  for (int idx = lane; idx < B * B; idx += 32) {
+__device__ __forceinline__ void load_tile_group(const FactorArgs& a, int I, int J, double* s, int pt) {
+#pragma unroll 4
+  for (int idx = pt; idx < B * B; idx += 96) {
     const int i = idx % B, j = idx / B;
     const int gi = I * B + i, gj = J * B + j, d = gi - gj;
     s[j * B + i] = (gi < a.n && d >= 0 && d <= a.k) ? __ldcg(a.ab + d + (long long)gj * a.ldab) : 0.0;
@@ -154,81 +172,87 @@ __device__ void diag_publisher(const FactorArgs& a, DiagSmem<B, F32>& sm, int la
   }
 }
 
-// ----------------------------------------------------------- prefetcher (warp 5)
+// ------------------------------------------------------- prefetcher (warps 5-7)
 // For step s: waits until the other CTAs have applied every update of A(s, s)
 // and A(s, s-1) except the step s-1 DSYRK (steps s0(s) .. s-2), and copies both
 // tiles into buffer s & 1 (free once step s-2 is finished).  A(s, s) is usually
-// ready first: its last outside update comes a step earlier.
+// ready first: its last outside update comes a step earlier.  One thread
+// waits; the three warps copy.
 template <int B, bool F32>
-__device__ void diag_prefetcher(const FactorArgs& a, DiagSmem<B, F32>& sm, int lane) {
+__device__ void diag_prefetcher(const FactorArgs& a, DiagSmem<B, F32>& sm, int pt) {
   const uint64_t limit = 4 * a.wait_ns;
+  bool failed = false;
   for (int s = 0; s < a.S; ++s) {
     const int cur = s & 1;
     const int s0 = first_step(a, s);
     const bool has_x = s >= 1 && a.p >= 1;
-    int ok = 1;
-    if (lane == 0) {
+    if (pt == 0) {
+      int ok = 1;
       if (s >= 2) ok = wait_smem_geq(&sm.consumed, s - 1, &sm.stop, a.ctl, a.status, limit);
       if (ok) ok = wait_tile_poll(a, s, s, has_x ? s - 1 - s0 : s - s0);
+      sm.pf_ok_d = ok;
     }
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    __syncwarp();
-    if (!ok) break;
-    load_tile_lanes<B>(a, s, s, sm.D[cur], lane);
+    bar_sync(kBarPF, 96);
+    if (!sm.pf_ok_d) {
+      failed = true;
+      break;
+    }
+    load_tile_group<B>(a, s, s, sm.D[cur], pt);
     if (has_x) {
-      if (lane == 0) ok = wait_tile_poll(a, s, s - 1, s - 1 - s0);
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      __syncwarp();
-      if (!ok) break;
-      load_tile_lanes<B>(a, s, s - 1, sm.X[cur], lane);
+      if (pt == 0) sm.pf_ok_x = wait_tile_poll(a, s, s - 1, s - 1 - s0);
+      bar_sync(kBarPF, 96);
+      if (!sm.pf_ok_x) {
+        failed = true;
+        break;
+      }
+      load_tile_group<B>(a, s, s - 1, sm.X[cur], pt);
     }
-    __syncwarp();
-    if (lane == 0) st_release_cta(&sm.in_ready, s + 1);
+    bar_sync(kBarPF, 96);
+    if (pt == 0) st_release_cta(&sm.in_ready, s + 1);
   }
-  if (lane == 0) {
-    // a failed wait (timeout or abort) ends the chain
-    if (ld_acquire_cta(&sm.in_ready) < a.S) *(volatile int*)&sm.stop = 1;
-  }
+  // a failed wait (timeout or abort) ends the chain
+  if (failed && pt == 0) *(volatile int*)&sm.stop = 1;
 }
 
 // --------------------------------------------------------------------- TRSM
-// X := X L^{-T} with L = L(s-1, s-1) and r = 1/diag(L), in place.  Warp w owns
-// rows w*B/4 ..; G lanes share a row, lane g keeps columns g, g+G, ... in
-// registers; column j is finished by its owner and shuffled to the row group.
-// (A product with an explicit L^{-1} would drop the substitution chain, but
-// forming L^{-1} inside POTRF costs the chain CTA more than it saves here.)
+// X := X L^{-T} with L = L(s-1, s-1) = U diag(1/r): the rows of Z = X diag(1/r)
+// solve the unit lower system Z U^T = A by substitution without divisions,
+// and X = Z diag(r) at the end.  Warp w owns rows w*B/4 ..; G lanes share a
+// row, lane g keeps columns g, g+G, ... in registers; column j, final when the
+// sweep reaches it, is shuffled to the row group.  Each step of the chain is
+// one shuffle and one DFMA.  (A product with an explicit L^{-1} would drop the
+// chain altogether, but forming L^{-1} inside POTRF costs the chain CTA more
+// than it saves here.)
 template <int B, typename VT, bool F32>
 __device__ __forceinline__ void diag_trsm(DiagSmem<B, F32>& sm, double* X, int tid) {
   constexpr int RPW = B / 4, G = 32 / RPW, C = B / G;
   const int warp = tid >> 5, lane = tid & 31;
   const int i = warp * RPW + lane / G, g = lane % G;
-  const VT* Lm;
-  if constexpr (F32) Lm = sm.Lf; else Lm = sm.L;
+  const VT* Um;
+  if constexpr (F32) Um = sm.Uf; else Um = sm.U;
   VT acc[C];
 #pragma unroll
   for (int c = 0; c < C; ++c) acc[c] = (VT)X[(g + G * c) * B + i];
 #pragma unroll
-  for (int j = 0; j < B; ++j) {
+  for (int j = 0; j < B - 1; ++j) {
     const int go = j % G, co = j / G;
-    if constexpr (F32) {
-      if (g == go) acc[co] *= sm.rf[j];
-    } else {
-      if (g == go) acc[co] *= sm.r[j];
-    }
-    const VT x = __shfl_sync(0xffffffffu, acc[co], go, G);
+    const VT z = __shfl_sync(0xffffffffu, acc[co], go, G);
 #pragma unroll
     for (int c = co; c < C; ++c) {
       const int l = g + G * c;
       if (l > j) {
-        if constexpr (F32) acc[c] = fmaf(-x, Lm[j * B + l], acc[c]);
-        else acc[c] = fma(-x, Lm[j * B + l], acc[c]);
+        if constexpr (F32) acc[c] = fmaf(-z, Um[j * B + l], acc[c]);
+        else acc[c] = fma(-z, Um[j * B + l], acc[c]);
       }
     }
   }
 #pragma unroll
   for (int c = 0; c < C; ++c) {
-    X[(g + G * c) * B + i] = (double)acc[c];
-    if constexpr (F32) sm.Xf[(g + G * c) * B + i] = (float)acc[c];
+    const int l = g + G * c;
+    VT v;
+    if constexpr (F32) v = acc[c] * sm.rf[l]; else v = acc[c] * sm.r[l];
+    X[l * B + i] = (double)v;
+    if constexpr (F32) sm.Xf[l * B + i] = (float)v;
   }
 }
 
@@ -274,18 +298,22 @@ __device__ __forceinline__ void diag_syrk(DiagSmem<B, F32>& sm, const double* X,
 
 // -------------------------------------------------------------------- POTRF
 // Cholesky of D (jmax valid columns) by the Schur recurrence without square
-// roots on the chain: with d_j the j-th pivot and y = D(:, j) / d_j,
-//     D(i, l) -= y_i D(l, j)   (j < l <= i),   d_{j+1} = D(j+1, j+1) - D(j+1, j)^2 / d_j,
+// roots on the chain: with d_j the j-th pivot and U(i, j) = D(i, j) / d_j,
+//     D(i, l) -= U(i, j) D(l, j)   (j < l <= i),   d_{j+1} = D(j+1, j+1) - D(j+1, j)^2 / d_j,
 // and L(i, j) = D(i, j) r_j with r_j = 1/sqrt(d_j) afterwards (all square
 // roots in one batch once the chain is done).  Warp 0 lane 0 runs only the
-// pivot recurrence (one DFMA and one division per column), alone on its
-// sub-partition; warps 1-3 form y and apply the rank-1 update one column
-// behind (two entries per thread at a time, so their loads and FMAs overlap).
-// D(j+1, j+1) and q_{j+1} = D(j+1, j)^2 reach the recurrence through shared
-// memory; the recurrence's own entry D(j+1, j+1) is left out of column j's update.
+// pivot recurrence (one DFMA and one reciprocal per column), alone on its
+// sub-partition; warps 1-3 form column j of U and apply the rank-1 update one
+// column behind (two entries per thread at a time, so their loads and FMAs
+// overlap).  D(j+1, j+1) and q_{j+1} = D(j+1, j)^2 reach the recurrence through
+// shared memory; the recurrence's own entry D(j+1, j+1) is left out of column
+// j's update.  U is kept for the next step's TRSM.  (Posting the next pivot's
+// two entries ahead of the rest of the column was measured slower: the update
+// warps, not the recurrence, then set the pace.)
 template <int B, bool F32>
 __device__ __forceinline__ void diag_potrf(DiagSmem<B, F32>& sm, double* D, int jmax, int tid) {
   const int warp = tid >> 5, lane = tid & 31;
+  double* U = sm.U;
   if (warp == 0) {
     double inv = 0.0;
     if (lane == 0) {
@@ -293,7 +321,7 @@ __device__ __forceinline__ void diag_potrf(DiagSmem<B, F32>& sm, double* D, int 
       if (jmax >= 2) sm.q[1] = D[1] * D[1];
       if (!(d > 0.0)) sm.fail = 1;
       sm.d[0] = d;
-      inv = 1.0 / d;
+      inv = pivot_rcp(d);
       sm.inv[0] = inv;
     }
     bar_arrive(kBarP, 128);
@@ -303,7 +331,7 @@ __device__ __forceinline__ void diag_potrf(DiagSmem<B, F32>& sm, double* D, int 
         const double d = fma(-sm.q[j + 1], inv, D[(j + 1) * B + j + 1]);
         if (!(d > 0.0) && sm.fail == 0) sm.fail = j + 2;
         sm.d[j + 1] = d;
-        inv = 1.0 / d;
+        inv = pivot_rcp(d);
         sm.inv[j + 1] = inv;
       }
       bar_arrive(kBarP + ((j + 1) & 1), 128);
@@ -315,7 +343,7 @@ __device__ __forceinline__ void diag_potrf(DiagSmem<B, F32>& sm, double* D, int 
       bar_sync(kBarP + (j & 1), 128);
       if (j + 1 < jmax) {
         const double inv = sm.inv[j];
-        for (int i = j + 1 + u; i < jmax; i += 96) sm.y[i] = D[j * B + i] * inv;
+        for (int i = j + 1 + u; i < jmax; i += 96) U[j * B + i] = D[j * B + i] * inv;
         bar_sync(kBarW, 96);
         const int T = (B - 1 - j) * (B - j) / 2;
         for (int e = u; e < T; e += 192) {
@@ -324,8 +352,8 @@ __device__ __forceinline__ void diag_potrf(DiagSmem<B, F32>& sm, double* D, int 
           const int i1 = c1 & 0xff, l1 = c1 >> 8, i2 = c2 & 0xff, l2 = c2 >> 8;
           const bool ok1 = i1 < jmax && !(i1 == j + 1 && l1 == j + 1);
           const bool ok2 = e2 < T && i2 < jmax && !(i2 == j + 1 && l2 == j + 1);
-          const double a1 = D[l1 * B + i1], x1 = D[j * B + l1], y1 = sm.y[i1];
-          const double a2 = D[l2 * B + i2], x2 = D[j * B + l2], y2 = sm.y[i2];
+          const double a1 = D[l1 * B + i1], x1 = D[j * B + l1], y1 = U[j * B + i1];
+          const double a2 = D[l2 * B + i2], x2 = D[j * B + l2], y2 = U[j * B + i2];
           const double v1 = fma(-y1, x1, a1);
           const double v2 = fma(-y2, x2, a2);
           if (ok1) {
@@ -381,17 +409,14 @@ __device__ void diag_compute(const FactorArgs& a, DiagSmem<B, F32>& sm, int tid)
     if constexpr (F32) {
       if (tid < B) sm.rf[tid] = (float)sm.r[tid];
     }
-    // L(i, j) = D(i, j) r_j and L(j, j) = d_j r_j: into shared memory for the
-    // next step's TRSM and into the band
+    // L(i, j) = D(i, j) r_j and L(j, j) = d_j r_j, formed as they are stored
     for (int idx = tid; idx < B * B; idx += 128) {
       const int i = idx % B, j = idx / B;
       if (i >= j && i < jmax) {
         const double rj = sm.r[j];
-        const double lv = (i == j) ? sm.d[j] * rj : D[idx] * rj;
-        sm.L[idx] = lv;
-        if constexpr (F32) sm.Lf[idx] = (float)lv;
         const int gi = s * B + i, gj = s * B + j, dd = gi - gj;
-        if (dd <= a.k) a.ab[dd + (long long)gj * a.ldab] = lv;
+        if (dd <= a.k) a.ab[dd + (long long)gj * a.ldab] = (i == j) ? sm.d[j] * rj : D[idx] * rj;
+        if constexpr (F32) sm.Uf[idx] = (float)sm.U[idx];
       }
     }
     bar_sync(kBarC, 128);
@@ -407,7 +432,6 @@ template <int B, bool F32>
 __device__ void diag_chain(const FactorArgs& a, DiagSmem<B, F32>& sm) {
   static_assert(B == 16 || B == 32, "the diagonal chain supports tiles of 16 and 32");
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (warp >= 6) return;
   if (tid == 0) {
     sm.in_ready = 0;
     sm.consumed = 0;
@@ -416,7 +440,7 @@ __device__ void diag_chain(const FactorArgs& a, DiagSmem<B, F32>& sm) {
     sm.fail = 0;
   }
   // triangle table: column l holds B - l entries, columns ordered B-1, B-2, ..., 0
-  for (int e = tid; e < B * (B + 1) / 2; e += 192) {
+  for (int e = tid; e < B * (B + 1) / 2; e += kThreads) {
     int l = B - 1, off = 0;
     while (e >= off + (B - l)) {
       off += B - l;
@@ -425,11 +449,11 @@ __device__ void diag_chain(const FactorArgs& a, DiagSmem<B, F32>& sm) {
     const int i = l + (e - off);
     sm.tri[e] = (unsigned short)((l << 8) | i);
   }
-  bar_sync(kBarInit, 192);
+  bar_sync(kBarInit, kThreads);
   if (warp == 4) {
     diag_publisher<B, F32>(a, sm, lane);
-  } else if (warp == 5) {
-    diag_prefetcher<B, F32>(a, sm, lane);
+  } else if (warp >= 5) {
+    diag_prefetcher<B, F32>(a, sm, tid - 160);
   } else {
     diag_compute<B, F32>(a, sm, tid);
   }

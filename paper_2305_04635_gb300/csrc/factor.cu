@@ -90,6 +90,17 @@ __global__ void __launch_bounds__(kThreads, 2) factor_kernel(FactorArgs a) {
   }
 }
 
+__global__ void pivot_rcp_kernel(const double* x, double* y, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = pivot_rcp(x[i]);
+}
+
+cudaError_t launch_pivot_rcp(const double* x, double* y, int n, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  pivot_rcp_kernel<<<(n + 255) / 256, 256, 0, stream>>>(x, y, n);
+  return cudaGetLastError();
+}
+
 FactorPlan make_factor_plan(int n, int k, int b) {
   FactorPlan P;
   P.n = n;

@@ -182,9 +182,11 @@ __device__ bool task_upd(const FactorArgs& a, int I, int J, int s, Smem<B>& sm, 
   constexpr int R = B / 16;
   const int tid = threadIdx.x;
   const int s0I = first_step(a, I);
+  // L_Is and A_IJ are usually final first; L_Js of the next block column comes
+  // last (for UPD(I, s+1, s) it is the diagonal chain's TRSM), so it is waited
+  // for and loaded after the others are already in flight.
   if (tid == 0) {
     bool ok = wait_tile(a, I, s, s - s0I + 1);
-    if (ok && J != I) ok = wait_tile(a, J, s, s - first_step(a, J) + 1);
     if (ok) ok = wait_tile(a, I, J, s - s0I);
     *s_flag = ok;
   }
@@ -193,8 +195,6 @@ __device__ bool task_upd(const FactorArgs& a, int I, int J, int s, Smem<B>& sm, 
   double* sA = sm.t0;
   double* sB = sm.t1;
   load_tile<B, kThreads>(a.ab, a.ldab, a.n, a.k, I, s, sA);
-  if (J != I) load_tile<B, kThreads>(a.ab, a.ldab, a.n, a.k, J, s, sB);
-  const double* sBr = (J != I) ? sB : sA;
   const int ty = tid / 16, tx = tid % 16;
   const bool diag = (I == J);
   double acc[R][R];
@@ -206,6 +206,14 @@ __device__ bool task_upd(const FactorArgs& a, int I, int J, int s, Smem<B>& sm, 
       const int d = gi - gj;
       acc[r][c] = (gi < a.n && d >= 0 && d <= a.k) ? __ldcg(a.ab + d + (long long)gj * a.ldab) : 0.0;
     }
+  if (J != I) {
+    __shared__ int s_ok_j;  // not s_flag: other threads may still be reading that one
+    if (tid == 0) s_ok_j = wait_tile(a, J, s, s - first_step(a, J) + 1);
+    __syncthreads();
+    if (!s_ok_j) return false;
+    load_tile<B, kThreads>(a.ab, a.ldab, a.n, a.k, J, s, sB);
+  }
+  const double* sBr = (J != I) ? sB : sA;
   __syncthreads();
 #pragma unroll 4
   for (int l = 0; l < B; ++l) {

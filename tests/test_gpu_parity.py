@@ -7,6 +7,8 @@ multiply-adds, reciprocal square roots and a different summation order from
 the oracle, so agreement is to rounding, never bitwise.  Each test prints
 the measured errors.
 """
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -204,3 +206,20 @@ def test_full_size_sampled(k):
     print(f"n={n} k={k}: rel err L {eL:.2e}, sampled backward err {be:.2e}, rel err x {ex:.2e}, "
           f"max sampled residual {np.abs(res).max():.2e}")
     assert eL <= TOL_L and be <= TOL_BE and ex <= TOL_X
+
+
+def test_pivot_reciprocal_against_division():
+    """The refined reciprocal of the pivot recurrence against IEEE division over the pivots' range."""
+    rng = np.random.default_rng(3)
+    x = np.ldexp(1.0 + rng.random(1 << 16), rng.integers(-60, 60, 1 << 16))
+    x[:4] = [1.0, 2.0, 0.75, 1e-12]
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    h = bchol.Handle()
+    assert h._lib.bchol_check_pivot_rcp(h.ptr, ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(yd.data_ptr()),
+                                        int(x.size)) == 0
+    y = yd.cpu().numpy()
+    rel = np.abs(y * x - 1.0)
+    ulps = np.abs(y - 1.0 / x) / np.spacing(1.0 / x)
+    print(f"pivot reciprocal: max |y x - 1| = {rel.max():.2e}, max error {ulps.max():.1f} ulp")
+    assert rel.max() <= 4 * 2.0 ** -52 and ulps.max() <= 4
