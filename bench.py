@@ -49,6 +49,10 @@ KS = [50, 100, 200, 500, 1000, 2000]
 FP64_PEAK_TFLOPS = 1.25
 HBM_FALLBACK_GBS = 6800.0
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) of one factor launch at n = 20000 for each sweep k, from
+# an ncu capture of dram__bytes_read.sum + dram__bytes_write.sum of this kernel;
+# traffic is proportional to n at fixed k, so it is scaled by n / 20000.
+TRAFFIC_N20000 = {50: 8.4e6, 100: 16.9e6, 200: 35.5e6, 500: 105.6e6, 1000: 258.5e6, 2000: 565.9e6}
 
 
 def measured_hbm_gbs() -> tuple[float, str]:
@@ -232,7 +236,9 @@ def run_ours(args, rank: int, world: int, dev: int):
         per_k[str(k)] = {"factor_ms": round(fm, 4), "solve_ms": round(sm, 4),
                          "factor_gflops_eq1": round(flops_eq1(n, k) / fm / 1e6, 2),
                          "factor_gflops_nk2": round(flops_nk2(n, k) / fm / 1e6, 2),
-                         "frac_fp64_roofline": round(roof / fm, 4)}
+                         "frac_fp64_roofline": round(roof / fm, 4),
+                         "dram_bytes": (round(TRAFFIC_N20000[k] * n / 20000) if k in TRAFFIC_N20000 else None),
+                         "algorithmic_bytes": 16 * (k + 1) * n}
         tot_flop += flops_nk2(n, k) * len(fac_ms[k])
         tot_ms += sum(fac_ms[k])
     achieved_tflops = tot_flop / (tot_ms * 1e-3) / 1e12
@@ -251,7 +257,11 @@ def run_ours(args, rank: int, world: int, dev: int):
                 "h2d_bytes_per_step": sum(8 * (k + 1) * n + 8 * n for k in ks),
                 "d2h_bytes_per_step": sum(8 * n + 4 for k in ks)},
         "roofline": {"bound": "alu", "achieved": round(achieved_tflops, 4), "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": round(achieved_tflops / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                     "unit": "TFLOP/s", "frac": round(achieved_tflops / FP64_PEAK_TFLOPS, 4),
+                     "traffic": (round(sum(TRAFFIC_N20000[k] for k in ks) * n / 20000 / len(ks))
+                                 if all(k in TRAFFIC_N20000 for k in ks) else None),
+                     "traffic_note": "DRAM bytes per factor launch, mean over the sweep's launches (ncu capture at "
+                                     "n = 20000, scaled by n); per-k figures in per_k",
                      "kernel": "factor_kernel", "flops_per_launch": "n*k^2",
                      "peak_source": "FP64 nominal from unit counts and clock (alu)"},
         "gpu_launches": launches_per_step * args.steps,
