@@ -244,6 +244,16 @@ bchol_status_t bchol_set_stall_tile(bchol_handle_t handle, int I, int J);
 long long bchol_plan_task_count(int n, int k, int tile);
 bchol_status_t bchol_plan_task(int n, int k, int tile, long long ticket, int* type, int* s, int* I, int* J);
 
+/* The task order of the adjoint's selected inversion (bchol_backward), for
+ * tests: the number of tasks for (n, k, tile) (or -1 on bad arguments), and
+ * ticket -> (type, J, I, g) in tile units: type 0 = FAR(I, J, group g) (far
+ * terms of P_IJ = sum_M Sigma_IM L_MJ), 1 = NEAR(I, J) (Sigma_IJ and its share of
+ * E_J), 2 = DIAG(J) (the diagonal tile); block columns J run from last to first
+ * (the Takahashi recurrences of the inverse's band; the paper's interior-point
+ * motivation, Sec. 1).  tile is 16, 32 or 64. */
+long long bchol_adjoint_plan_task_count(int n, int k, int tile);
+bchol_status_t bchol_adjoint_plan_task(int n, int k, int tile, long long ticket, int* type, int* J, int* I, int* g);
+
 /* Self-check of the reciprocal the diagonal POTRF's pivot recurrence uses
  * (d_{j+1} = A(j+1,j+1) - A(j+1,j)^2 / d_j, the Schur complement of Sec. 3's
  * POTRF step): y[i] = 1/x[i] by that routine, for n device doubles x (n >= 0;

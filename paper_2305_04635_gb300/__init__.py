@@ -85,6 +85,8 @@ def load_library():
         "bchol_plan_task_count": ([I, I, I], ctypes.c_longlong),
         "bchol_plan_task": ([I, I, I, ctypes.c_longlong, P, P, P, P], I),
         "bchol_check_pivot_rcp": ([P, P, P, I], I),
+        "bchol_adjoint_plan_task_count": ([I, I, I], ctypes.c_longlong),
+        "bchol_adjoint_plan_task": ([I, I, I, ctypes.c_longlong, P, P, P, P], I),
         "bchol_version": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -269,6 +271,21 @@ def plan_tasks(n: int, k: int, tile: int) -> list[tuple[int, int, int, int]]:
         _check("bchol_plan_task", lib.bchol_plan_task(n, k, tile, ticket, ctypes.byref(t), ctypes.byref(s),
                                                       ctypes.byref(I), ctypes.byref(J)))
         out.append((t.value, s.value, I.value, J.value))
+    return out
+
+
+def adjoint_plan_tasks(n: int, k: int, tile: int) -> list[tuple[int, int, int, int]]:
+    """The selected inversion's task order as (type, J, I, g) (see bchol_adjoint_plan_task)."""
+    lib = load_library()
+    cnt = lib.bchol_adjoint_plan_task_count(n, k, tile)
+    if cnt < 0:
+        raise ValueError("bad arguments")
+    out = []
+    t, J, I, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    for ticket in range(cnt):
+        _check("bchol_adjoint_plan_task", lib.bchol_adjoint_plan_task(n, k, tile, ticket, ctypes.byref(t),
+                                                                      ctypes.byref(J), ctypes.byref(I), ctypes.byref(g)))
+        out.append((t.value, J.value, I.value, g.value))
     return out
 
 

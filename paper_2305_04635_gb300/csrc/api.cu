@@ -177,6 +177,20 @@ bchol_status_t bchol_plan_task(int n, int k, int tile, long long ticket, int* ty
   return BCHOL_OK;
 }
 
+long long bchol_adjoint_plan_task_count(int n, int k, int tile) {
+  if (n < 0 || k < 0 || !(tile == 16 || tile == 32 || tile == 64)) return -1;
+  const int kk = (n > 0 && k > n - 1) ? n - 1 : k;
+  return adjoint_plan_count(n, kk, tile);
+}
+
+bchol_status_t bchol_adjoint_plan_task(int n, int k, int tile, long long ticket, int* type, int* J, int* I, int* g) {
+  if (n < 0 || k < 0 || !(tile == 16 || tile == 32 || tile == 64) || !type || !J || !I || !g) return BCHOL_ERR_ARG;
+  const int kk = (n > 0 && k > n - 1) ? n - 1 : k;
+  if (ticket < 0 || ticket >= adjoint_plan_count(n, kk, tile)) return BCHOL_ERR_ARG;
+  adjoint_plan_task(n, kk, tile, ticket, type, J, I, g);
+  return BCHOL_OK;
+}
+
 bchol_status_t bchol_check_pivot_rcp(bchol_handle_t h, const double* x, double* y, int n) {
   if (!h || n < 0 || (n > 0 && (!x || !y))) return BCHOL_ERR_ARG;
   if (launch_pivot_rcp(x, y, n, h->stream) != cudaSuccess) {

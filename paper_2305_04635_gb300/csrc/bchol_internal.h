@@ -49,6 +49,8 @@ int num_sms();
 
 // Adjoint (selinv.cu): band of A^{-1} by selected inversion and the band gradient.
 size_t selinv_workspace_bytes(int n, int k, int b);
+long long adjoint_plan_count(int n, int k, int b);
+void adjoint_plan_task(int n, int k, int b, long long t, int* type, int* J, int* I, int* g);
 cudaError_t launch_backward(int n, int k, int b, const double* L, long long ldl, const double* x, const double* bbar,
                             double ldbar, double* g, long long ldg, void* ws, int* status, uint64_t wait_ns,
                             int ctas_per_sm, cudaStream_t stream);

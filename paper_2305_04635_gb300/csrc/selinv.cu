@@ -11,96 +11,149 @@
 //     abar(i,i) =   ldbar Sigma(i,i) -  bbar_i x_i.
 // Only the band of Sigma is needed.  It follows from Sigma L = L^{-T} (the
 // Takahashi recurrences), walked over b x b tiles from the last block column
-// to the first; every quantity below stays inside the band:
-//     SACC(I,J,M)  P_IJ += Sigma_IM L_MJ          (M = J+m .. J+1, descending)
-//     SFIN(I,J)    Sigma_IJ = -P_IJ L_JJ^{-1}      (back substitution on L_JJ)
-//     DACC(J,M)    E_J  += Sigma_MJ^T L_MJ         (lower triangle, M descending)
-//     DFIN(J)      the diagonal tile, column by column from the right:
-//                  Sigma_ij = -(E_ij + sum_{m in tile, m>j} L_mj Sigma_im) / L_jj   (i > j)
-//                  Sigma_jj = (1/L_jj - E_jj - sum_{i in tile, i>j} L_ij Sigma_ij) / L_jj
-// P_IJ and E_J accumulate in the output band array itself (its tile slots),
-// so no extra storage is needed.  The walk is a persistent kernel with the
-// same ticket / ready-counter protocol as the factorization.
+// to the first; every quantity below stays inside the band.  For block column
+// J with m = min(p, S-1-J) tiles below the diagonal:
+//     P_IJ   = sum_{M=J+1..J+m} Sigma_IM L_MJ           (I = J+1..J+m)
+//     Sigma_IJ = -P_IJ L_JJ^{-1}                         (back substitution on L_JJ)
+//     E_J    = sum_{I=J+1..J+m} Sigma_IJ^T L_IJ          (lower triangle)
+//     the diagonal tile, column by column from the right:
+//       Sigma_ij = -(E_ij + sum_{l in tile, l>j} L_lj Sigma_il) / L_jj   (i > j)
+//       Sigma_jj = (1/L_jj - E_jj - sum_{i in tile, i>j} L_ij Sigma_ij) / L_jj
+// Tasks (a persistent launch with the factorization's ticket / ready-counter
+// protocol):
+//     FAR(I,J,g)  the terms M = J+2.. of P_IJ, in groups of kFarGroup, each
+//                 into its own partial tile (no chain between the groups).
+//                 For I >= J+2 they read only block columns >= J+2, so they
+//                 are ordered a column early; for I = J+1 they wait for
+//                 column J+1.
+//     NEAR(I,J)   P_IJ = Sigma_{I,J+1} L_{J+1,J} + the partials, Sigma_IJ, and
+//                 its share Sigma_IJ^T L_IJ of E_J into a partial tile.
+//     DIAG(J)     E_J = sum of the shares, then the diagonal tile.
+// So one block column costs three dependent tasks (FAR of row J+1, NEAR,
+// DIAG) instead of accumulation chains of m tasks.  Partial tiles live in a
+// scratch ring of four block columns; a task of column J writes its slot only
+// once DIAG(J+4) is done, which implies that every reader of the slot's
+// previous contents (the NEAR tasks and DIAG of column J+4) has finished --
+// the NEAR tasks of far rows of column J need not otherwise wait for it.
 #include "../../include/bchol.h"
 #include "factor_tasks.cuh"
 
 namespace bchol {
 
+constexpr int kFarGroup = 4;   // terms of P_IJ per FAR task
+
 struct SelArgs {
   const double* L;   // factor band
   long long ldl;
-  double* sig;       // output band: Sigma (accumulators first)
+  double* sig;       // output band: Sigma
   long long lds;
   int n, k, S, p;
+  int ngmax;         // FAR groups per tile at m = p
   unsigned long long total;
-  int* flags;
+  int* flags;        // [tiles: Sigma final] [tiles: FAR partials done] [columns: E shares done]
+  double* part;      // FAR partials: [4 columns][p rows][ngmax][b*b]
+  double* wsh;       // E shares:     [4 columns][p rows][b*b]
   Control* ctl;
   int* status;
   uint64_t wait_ns;
 };
 
-enum SelType { kSacc = 0, kSfin = 1, kDacc = 2, kDfin = 3 };
+enum SelType { kFar = 0, kNear = 1, kDiag = 2 };
 
 __host__ __device__ inline int sel_m(int S, int p, int J) { return (p < S - 1 - J) ? p : S - 1 - J; }
+__host__ __device__ inline int sel_ng(int m) { return m >= 2 ? (m - 1 + kFarGroup - 1) / kFarGroup : 0; }
 
-// Ticket -> task.  Block column J = S-1, S-2, ..., 0 has m = sel_m(J) and
-// (m+1)^2 tasks: m*m SACC (M-major, M descending), m SFIN, m DACC, 1 DFIN.
-__host__ __device__ inline void sel_decode(int S, int p, long long t, int& type, int& J, int& I, int& M) {
-  int jb = 0;
-  const int head = (p < S) ? p : S;   // leading blocks with m = jb < p
-  long long r = t;
-  while (jb < head) {
-    const long long sz = (long long)(jb + 1) * (jb + 1);
-    if (r < sz) break;
-    r -= sz;
-    ++jb;
-  }
-  if (jb == head) {
-    const long long sz = (long long)(p + 1) * (p + 1);
-    jb += (int)(r / sz);
-    r %= sz;
-  }
-  J = S - 1 - jb;
+// Tickets of block column J, in processing order:
+//   FAR(J+1, J, g) (g < ng(m_J)), NEAR(J+1..J+m_J, J), DIAG(J),
+//   then FAR(I, J-2, g) for I = J..J-2+m_{J-2} (the early far terms of column J-2).
+__host__ __device__ inline long long sel_bsize(int S, int p, int J) {
   const int m = sel_m(S, p, J);
-  if (r < (long long)m * m) {
-    type = kSacc;
-    const int q = (int)(r / m);
-    M = J + m - q;
-    I = J + 1 + (int)(r % m);
+  long long sz = sel_ng(m) + m + 1;
+  if (J >= 2) {
+    const int m2 = sel_m(S, p, J - 2);
+    if (m2 >= 2) sz += (long long)(m2 - 1) * sel_ng(m2);
+  }
+  return sz;
+}
+
+// Ticket -> (type, J, I, g).  Columns J = S-1 .. 0; the columns with m_J = p and
+// m_{J-2} = p (2 <= J <= S-1-p) all have the same block size.
+__host__ __device__ inline void sel_decode(int S, int p, long long t, int& type, int& J, int& I, int& g) {
+  J = S - 1;
+  const int jreg_hi = S - 1 - p;  // regular columns: 2 .. jreg_hi
+  while (J > jreg_hi && J >= 0) {  // head: m_J < p
+    const long long bs = sel_bsize(S, p, J);
+    if (t < bs) break;
+    t -= bs;
+    --J;
+  }
+  if (J <= jreg_hi && J >= 2) {
+    const long long breg = sel_bsize(S, p, jreg_hi);
+    const long long nreg = (long long)jreg_hi - 1;  // columns jreg_hi .. 2
+    const long long d = t / breg;
+    if (d < nreg) {
+      J = jreg_hi - (int)d;
+      t -= d * breg;
+    } else {
+      t -= nreg * breg;
+      J = 1;
+    }
+  }
+  while (J < 2 && J >= 0) {  // tail: columns 1 and 0 (when not in the head)
+    const long long bs = sel_bsize(S, p, J);
+    if (t < bs) break;
+    t -= bs;
+    --J;
+  }
+  const int m = sel_m(S, p, J), ng = sel_ng(m);
+  if (t < ng) {
+    type = kFar;
+    I = J + 1;
+    g = (int)t;
     return;
   }
-  r -= (long long)m * m;
-  if (r < m) {
-    type = kSfin;
-    I = J + 1 + (int)r;
-    M = 0;
+  t -= ng;
+  if (t < m) {
+    type = kNear;
+    I = J + 1 + (int)t;
+    g = 0;
     return;
   }
-  r -= m;
-  if (r < m) {
-    type = kDacc;
-    M = J + m - (int)r;
+  t -= m;
+  if (t == 0) {
+    type = kDiag;
     I = J;
+    g = 0;
     return;
   }
-  type = kDfin;
-  I = J;
-  M = 0;
+  t -= 1;
+  const int J2 = J - 2, ng2 = sel_ng(sel_m(S, p, J2));
+  type = kFar;
+  I = J2 + 2 + (int)(t / ng2);
+  g = (int)(t % ng2);
+  J = J2;
 }
 
 unsigned long long sel_total(int S, int p) {
   unsigned long long t = 0;
-  for (int J = S - 1; J >= 0; --J) {
-    const unsigned long long m = (unsigned long long)sel_m(S, p, J);
-    t += (m + 1) * (m + 1);
-  }
+  for (int J = S - 1; J >= 0; --J) t += (unsigned long long)sel_bsize(S, p, J);
   return t;
 }
 
 __device__ __forceinline__ int sfidx(const SelArgs& a, int I, int J) { return J * (a.p + 1) + (I - J); }
+__device__ __forceinline__ int* sig_flag(const SelArgs& a, int I, int J) { return &a.flags[sfidx(a, I, J)]; }
+__device__ __forceinline__ int* far_flag(const SelArgs& a, int I, int J) {
+  return &a.flags[a.S * (a.p + 1) + sfidx(a, I, J)];
+}
+__device__ __forceinline__ int* w_flag(const SelArgs& a, int J) { return &a.flags[2 * a.S * (a.p + 1) + J]; }
 
-__device__ __forceinline__ bool sel_wait(const SelArgs& a, int I, int J, int target) {
-  return wait_flag_geq(&a.flags[sfidx(a, I, J)], target, a.ctl, a.status, a.wait_ns);
+template <int B>
+__device__ __forceinline__ double* part_tile(const SelArgs& a, int I, int J, int g) {
+  return a.part + ((((size_t)(J & 3) * a.p + (I - J - 1)) * a.ngmax + g) * B * B);
+}
+template <int B>
+__device__ __forceinline__ double* w_tile(const SelArgs& a, int I, int J) {
+  return a.wsh + (((size_t)(J & 3) * a.p + (I - J - 1)) * B * B);
 }
 
 // Band element (gi, gj), gi >= gj, of an array (zero outside the band/matrix).
@@ -118,35 +171,21 @@ __device__ __forceinline__ void sput(const SelArgs& a, int gi, int gj, double v)
   if (gi < a.n && d >= 0 && d <= a.k) a.sig[d + (long long)gj * a.lds] = v;
 }
 
-// SACC(I,J,M): P_IJ += Sigma_IM L_MJ.  sX[l*B+i] = Sigma(I*B+i, M*B+l), sY[l*B+j] = L(M*B+l, J*B+j).
+// Release a counter after a CTA's stores: barrier, fence, one atomic add.
+__device__ __forceinline__ void publish_add(int* counter) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(counter, 1);
+  }
+}
+
+// acc (R x R per thread: rows ty+16r, columns tx+16c) += X Y with X, Y staged as
+// sX[l*B+i] = X(i, l), sY[l*B+j] = Y(l, j).
 template <int B>
-__device__ bool sel_sacc(const SelArgs& a, int I, int J, int M, Smem<B>& sm, int* s_flag) {
+__device__ __forceinline__ void tile_mma(const double* sX, const double* sY, double (&acc)[B / 16][B / 16], int ty,
+                                         int tx) {
   constexpr int R = B / 16;
-  const int tid = threadIdx.x;
-  const int m = sel_m(a.S, a.p, J);
-  const int q = J + m - M;   // position of M in the descending order
-  if (tid == 0) {
-    const int hi = I > M ? I : M, lo = I > M ? M : I;
-    bool ok = sel_wait(a, hi, lo, sel_m(a.S, a.p, lo) + 1);
-    if (ok) ok = sel_wait(a, I, J, q);
-    *s_flag = ok;
-  }
-  __syncthreads();
-  if (!*s_flag) return false;
-  double* sX = sm.t0;
-  double* sY = sm.t1;
-  for (int idx = tid; idx < B * B; idx += kThreads) {
-    const int i = idx % B, l = idx / B;
-    sX[l * B + i] = sget(a, I * B + i, M * B + l);
-    sY[l * B + i] = bget(a.L, a.ldl, a.n, a.k, M * B + l, J * B + i, false);   // (l, j = i)
-  }
-  const int ty = tid / 16, tx = tid % 16;
-  double acc[R][R];
-#pragma unroll
-  for (int r = 0; r < R; ++r)
-#pragma unroll
-    for (int c = 0; c < R; ++c) acc[r][c] = bget(a.sig, a.lds, a.n, a.k, I * B + ty + 16 * r, J * B + tx + 16 * c, true);
-  __syncthreads();
 #pragma unroll 4
   for (int l = 0; l < B; ++l) {
     double xv[R], yv[R];
@@ -159,70 +198,65 @@ __device__ bool sel_sacc(const SelArgs& a, int I, int J, int M, Smem<B>& sm, int
 #pragma unroll
       for (int c = 0; c < R; ++c) acc[r][c] = fma(xv[r], yv[c], acc[r][c]);
   }
+}
+
+// FAR(I,J,g): partial = sum over M in group g of Sigma_IM L_MJ.
+template <int B>
+__device__ bool sel_far(const SelArgs& a, int I, int J, int g, Smem<B>& sm, int* s_flag) {
+  constexpr int R = B / 16;
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  const int m = sel_m(a.S, a.p, J);
+  const int mlo = J + 2 + g * kFarGroup, mhi = min(J + 1 + (g + 1) * kFarGroup, J + m);
+  double acc[R][R];
 #pragma unroll
   for (int r = 0; r < R; ++r)
 #pragma unroll
-    for (int c = 0; c < R; ++c) sput(a, I * B + ty + 16 * r, J * B + tx + 16 * c, acc[r][c]);
-  publish(&a.flags[sfidx(a, I, J)], q + 1);
+    for (int c = 0; c < R; ++c) acc[r][c] = 0.0;
+  double* sX = sm.t0;
+  double* sY = sm.t1;
+  for (int M = mlo; M <= mhi; ++M) {
+    if (tid == 0) *s_flag = wait_flag_geq(sig_flag(a, max(I, M), min(I, M)), 1, a.ctl, a.status, a.wait_ns);
+    __syncthreads();
+    if (!*s_flag) return false;
+    for (int idx = tid; idx < B * B; idx += kThreads) {
+      const int i = idx % B, l = idx / B;
+      sX[l * B + i] = sget(a, I * B + i, M * B + l);
+      sY[l * B + i] = bget(a.L, a.ldl, a.n, a.k, M * B + l, J * B + i, false);   // (l, j = i)
+    }
+    __syncthreads();
+    tile_mma<B>(sX, sY, acc, ty, tx);
+    __syncthreads();
+  }
+  if (J + 4 < a.S) {  // the scratch slot's previous column is finished
+    if (tid == 0) *s_flag = wait_flag_geq(sig_flag(a, J + 4, J + 4), 1, a.ctl, a.status, a.wait_ns);
+    __syncthreads();
+    if (!*s_flag) return false;
+  }
+  double* out = part_tile<B>(a, I, J, g);
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int c = 0; c < R; ++c) out[(tx + 16 * c) * B + ty + 16 * r] = acc[r][c];
+  publish_add(far_flag(a, I, J));
   return true;
 }
 
-// SFIN(I,J): Sigma_IJ = -P_IJ L_JJ^{-1}, row by row (back substitution over columns, right to left).
+// NEAR(I,J): Sigma_IJ = -(Sigma_{I,J+1} L_{J+1,J} + FAR partials) L_JJ^{-1}, then
+// its share Sigma_IJ^T L_IJ (lower triangle) of E_J.
 template <int B>
-__device__ bool sel_sfin(const SelArgs& a, int I, int J, Smem<B>& sm, int* s_flag) {
-  constexpr int TPR = kThreads / B;
-  constexpr int R = B / TPR;
-  __shared__ double s_rinv[B];
-  const int tid = threadIdx.x;
-  const int m = sel_m(a.S, a.p, J);
-  if (tid == 0) *s_flag = sel_wait(a, I, J, m);
-  __syncthreads();
-  if (!*s_flag) return false;
-  double* sL = sm.t1;   // sL[j*B + l] = L(J*B+l, J*B+j)
-  for (int idx = tid; idx < B * B; idx += kThreads) {
-    const int l = idx % B, j = idx / B;
-    sL[j * B + l] = bget(a.L, a.ldl, a.n, a.k, J * B + l, J * B + j, false);
-  }
-  __syncthreads();
-  const int jmax = min(B, a.n - J * B);
-  if (tid < B) s_rinv[tid] = (tid < jmax) ? 1.0 / sL[tid * B + tid] : 0.0;
-  const int i = tid / TPR, sub = tid % TPR;
-  double acc[R];
-#pragma unroll
-  for (int qq = 0; qq < R; ++qq) acc[qq] = -bget(a.sig, a.lds, a.n, a.k, I * B + i, J * B + sub + qq * TPR, true);
-  __syncthreads();
-#pragma unroll
-  for (int jj = 0; jj < B; ++jj) {
-    const int j = B - 1 - jj;
-    const int owner = j % TPR, qj = j / TPR;
-    double x = 0.0;
-    if (sub == owner) {
-      x = acc[qj] * s_rinv[j];
-      acc[qj] = x;
-    }
-    x = __shfl_sync(0xffffffffu, x, owner, TPR);
-#pragma unroll
-    for (int qq = 0; qq <= qj; ++qq) {
-      const int l = sub + qq * TPR;
-      if (l < j) acc[qq] = fma(-x, sL[l * B + j], acc[qq]);   // L(j, l)
-    }
-  }
-#pragma unroll
-  for (int qq = 0; qq < R; ++qq) sput(a, I * B + i, J * B + sub + qq * TPR, acc[qq]);
-  publish(&a.flags[sfidx(a, I, J)], m + 1);
-  return true;
-}
-
-// DACC(J,M): E_J += Sigma_MJ^T L_MJ (lower triangle).  sX[l*B+i] = Sigma(M*B+l, J*B+i), sY[l*B+j] = L(M*B+l, J*B+j).
-template <int B>
-__device__ bool sel_dacc(const SelArgs& a, int J, int M, Smem<B>& sm, int* s_flag) {
+__device__ bool sel_near(const SelArgs& a, int I, int J, Smem<B>& sm, int* s_flag) {
   constexpr int R = B / 16;
-  const int tid = threadIdx.x;
-  const int m = sel_m(a.S, a.p, J);
-  const int q = J + m - M;
+  constexpr int TPR = kThreads / B;
+  constexpr int RS = B / TPR;
+  __shared__ double sP[B * B];
+  __shared__ double s_rinv[B];
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  const int m = sel_m(a.S, a.p, J), ng = sel_ng(m);
   if (tid == 0) {
-    bool ok = sel_wait(a, M, J, m + 1);
-    if (ok) ok = sel_wait(a, J, J, q);
+    bool ok = wait_flag_geq(far_flag(a, I, J), ng, a.ctl, a.status, a.wait_ns);
+    if (ok) ok = wait_flag_geq(sig_flag(a, I, J + 1), 1, a.ctl, a.status, a.wait_ns);
+    // the share's scratch slot: its previous column is finished
+    if (ok && J + 4 < a.S) ok = wait_flag_geq(sig_flag(a, J + 4, J + 4), 1, a.ctl, a.status, a.wait_ns);
     *s_flag = ok;
   }
   __syncthreads();
@@ -231,46 +265,99 @@ __device__ bool sel_dacc(const SelArgs& a, int J, int M, Smem<B>& sm, int* s_fla
   double* sY = sm.t1;
   for (int idx = tid; idx < B * B; idx += kThreads) {
     const int i = idx % B, l = idx / B;
-    sX[l * B + i] = bget(a.sig, a.lds, a.n, a.k, M * B + l, J * B + i, true);
-    sY[l * B + i] = bget(a.L, a.ldl, a.n, a.k, M * B + l, J * B + i, false);
+    sX[l * B + i] = sget(a, I * B + i, (J + 1) * B + l);   // Sigma_{I,J+1} (symmetric when I = J+1)
+    sY[l * B + i] = bget(a.L, a.ldl, a.n, a.k, (J + 1) * B + l, J * B + i, false);  // L_{J+1,J}
   }
-  const int ty = tid / 16, tx = tid % 16;
   double acc[R][R];
 #pragma unroll
   for (int r = 0; r < R; ++r)
 #pragma unroll
-    for (int c = 0; c < R; ++c) acc[r][c] = bget(a.sig, a.lds, a.n, a.k, J * B + ty + 16 * r, J * B + tx + 16 * c, true);
+    for (int c = 0; c < R; ++c) {
+      double v = 0.0;
+      for (int gg = 0; gg < ng; ++gg) v += __ldcg(part_tile<B>(a, I, J, gg) + (tx + 16 * c) * B + ty + 16 * r);
+      acc[r][c] = v;
+    }
   __syncthreads();
-#pragma unroll 4
-  for (int l = 0; l < B; ++l) {
-    double xv[R], yv[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) xv[r] = sX[l * B + ty + 16 * r];
-#pragma unroll
-    for (int c = 0; c < R; ++c) yv[c] = sY[l * B + tx + 16 * c];
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-#pragma unroll
-      for (int c = 0; c < R; ++c)
-        if (r >= c) acc[r][c] = fma(xv[r], yv[c], acc[r][c]);
-  }
+  tile_mma<B>(sX, sY, acc, ty, tx);
+  // P -> shared memory (sP[j*B + i]); L_JJ -> sY (sY[j*B + l] = L(J*B+l, J*B+j))
 #pragma unroll
   for (int r = 0; r < R; ++r)
 #pragma unroll
-    for (int c = 0; c < R; ++c) sput(a, J * B + ty + 16 * r, J * B + tx + 16 * c, acc[r][c]);
-  publish(&a.flags[sfidx(a, J, J)], q + 1);
+    for (int c = 0; c < R; ++c) sP[(tx + 16 * c) * B + ty + 16 * r] = acc[r][c];
+  __syncthreads();
+  for (int idx = tid; idx < B * B; idx += kThreads) {
+    const int l = idx % B, j = idx / B;
+    sY[j * B + l] = bget(a.L, a.ldl, a.n, a.k, J * B + l, J * B + j, false);
+  }
+  __syncthreads();
+  // Sigma_IJ = -P L_JJ^{-1}, row by row: back substitution over the columns, right to left
+  const int jmax = min(B, a.n - J * B);
+  if (tid < B) s_rinv[tid] = (tid < jmax) ? 1.0 / sY[tid * B + tid] : 0.0;
+  const int i = tid / TPR, sub = tid % TPR;
+  double sacc[RS];
+#pragma unroll
+  for (int qq = 0; qq < RS; ++qq) sacc[qq] = -sP[(sub + qq * TPR) * B + i];
+  __syncthreads();
+#pragma unroll
+  for (int jj = 0; jj < B; ++jj) {
+    const int j = B - 1 - jj;
+    const int owner = j % TPR, qj = j / TPR;
+    double x = 0.0;
+    if (sub == owner) {
+      x = sacc[qj] * s_rinv[j];
+      sacc[qj] = x;
+    }
+    x = __shfl_sync(0xffffffffu, x, owner, TPR);
+#pragma unroll
+    for (int qq = 0; qq <= qj; ++qq) {
+      const int l = sub + qq * TPR;
+      if (l < j) sacc[qq] = fma(-x, sY[l * B + j], sacc[qq]);   // L(j, l)
+    }
+  }
+  __syncthreads();   // every warp is done with L_JJ in sY before it is overwritten below
+  // store Sigma_IJ (band slots only) and keep the stored values (zero off the band) for the share
+#pragma unroll
+  for (int qq = 0; qq < RS; ++qq) {
+    const int gi = I * B + i, gj = J * B + sub + qq * TPR, d = gi - gj;
+    const bool in = gi < a.n && d >= 0 && d <= a.k;
+    if (in) a.sig[d + (long long)gj * a.lds] = sacc[qq];
+    sX[i * B + sub + qq * TPR] = in ? sacc[qq] : 0.0;   // sX[l*B + c] = Sigma_IJ(l, c)
+  }
+  for (int idx = tid; idx < B * B; idx += kThreads) {
+    const int l = idx % B, j = idx / B;
+    sY[l * B + j] = bget(a.L, a.ldl, a.n, a.k, I * B + l, J * B + j, false);   // sY[l*B + j] = L_IJ(l, j)
+  }
+  __syncthreads();
+  // share(c, j) = sum_l Sigma_IJ(l, c) L_IJ(l, j), lower triangle c >= j
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int c = 0; c < R; ++c) acc[r][c] = 0.0;
+  tile_mma<B>(sX, sY, acc, ty, tx);
+  double* out = w_tile<B>(a, I, J);
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int c = 0; c < R; ++c) out[(tx + 16 * c) * B + ty + 16 * r] = (ty + 16 * r >= tx + 16 * c) ? acc[r][c] : 0.0;
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    st_release(sig_flag(a, I, J), 1);
+    atomicAdd(w_flag(a, J), 1);
+  }
   return true;
 }
 
-// DFIN(J): the diagonal tile by the scalar recurrence, columns from right to left.
-// sS holds Sigma of the tile (full square, both triangles); sE holds E_J; sL the factor tile.
+// DIAG(J): E_J from the shares, then the diagonal tile by the scalar recurrence,
+// columns from right to left.  sS holds Sigma of the tile (full square, both
+// triangles); sE holds E_J; sL the factor tile.
 template <int B>
-__device__ bool sel_dfin(const SelArgs& a, int J, Smem<B>& sm, int* s_flag) {
+__device__ bool sel_diag(const SelArgs& a, int J, Smem<B>& sm, int* s_flag) {
   __shared__ double sE[B * B];
   __shared__ double s_part[B];
   const int tid = threadIdx.x;
   const int m = sel_m(a.S, a.p, J);
-  if (tid == 0) *s_flag = sel_wait(a, J, J, m);
+  if (tid == 0) *s_flag = wait_flag_geq(w_flag(a, J), m, a.ctl, a.status, a.wait_ns);
   __syncthreads();
   if (!*s_flag) return false;
   double* sS = sm.t0;   // sS[j*B + i] = Sigma(i, j), symmetric
@@ -278,7 +365,10 @@ __device__ bool sel_dfin(const SelArgs& a, int J, Smem<B>& sm, int* s_flag) {
   for (int idx = tid; idx < B * B; idx += kThreads) {
     const int i = idx % B, j = idx / B;
     sL[j * B + i] = bget(a.L, a.ldl, a.n, a.k, J * B + i, J * B + j, false);
-    sE[j * B + i] = (i >= j) ? bget(a.sig, a.lds, a.n, a.k, J * B + i, J * B + j, true) : 0.0;
+    double e = 0.0;
+    if (i >= j)
+      for (int ii = J + 1; ii <= J + m; ++ii) e += __ldcg(w_tile<B>(a, ii, J) + idx);
+    sE[j * B + i] = e;
     sS[j * B + i] = 0.0;
   }
   __syncthreads();
@@ -308,7 +398,7 @@ __device__ bool sel_dfin(const SelArgs& a, int J, Smem<B>& sm, int* s_flag) {
     const int i = idx % B, j = idx / B;
     if (i >= j && i < jmax) sput(a, J * B + i, J * B + j, sS[j * B + i]);
   }
-  publish(&a.flags[sfidx(a, J, J)], m + 1);
+  publish(sig_flag(a, J, J), 1);
   return true;
 }
 
@@ -326,17 +416,15 @@ __global__ void __launch_bounds__(kThreads, 2) selinv_kernel(SelArgs a) {
     const long long t = s_task;
     if (t >= (long long)a.total) break;
     if (threadIdx.x == 0) next = atomicAdd(&a.ctl->ticket, 1ULL);
-    int type, J, I, M;
-    sel_decode(a.S, a.p, t, type, J, I, M);
+    int type, J, I, g;
+    sel_decode(a.S, a.p, t, type, J, I, g);
     bool ok;
-    if (type == kSacc)
-      ok = sel_sacc<B>(a, I, J, M, sm, &s_flag);
-    else if (type == kSfin)
-      ok = sel_sfin<B>(a, I, J, sm, &s_flag);
-    else if (type == kDacc)
-      ok = sel_dacc<B>(a, J, M, sm, &s_flag);
+    if (type == kFar)
+      ok = sel_far<B>(a, I, J, g, sm, &s_flag);
+    else if (type == kNear)
+      ok = sel_near<B>(a, I, J, sm, &s_flag);
     else
-      ok = sel_dfin<B>(a, J, sm, &s_flag);
+      ok = sel_diag<B>(a, J, sm, &s_flag);
     if (!ok) break;
   }
 }
@@ -384,11 +472,21 @@ __global__ void __launch_bounds__(1024) logdet_kernel(const double* __restrict__
   if (threadIdx.x == 0) *out = 2.0 * red[0];
 }
 
+static int sel_ngmax(int p) { return p >= 2 ? (p - 1 + kFarGroup - 1) / kFarGroup : 1; }
+
+// control block | flags (2 S (p+1) + S ints, rounded to 256 B) | FAR partials | E shares
+static size_t sel_flag_bytes(int S, int p) {
+  const size_t f = sizeof(int) * ((size_t)2 * S * (p + 1) + S);
+  return (f + 255) / 256 * 256;
+}
+
 size_t selinv_workspace_bytes(int n, int k, int b) {
   const int S = (n + b - 1) / b;
   int p = (k + b - 1) / b;
   if (p > S - 1) p = S - 1;
-  return 256 + sizeof(int) * (size_t)S * (size_t)(p + 1);
+  if (p < 1) p = 1;
+  const size_t tile = sizeof(double) * (size_t)b * b;
+  return 256 + sel_flag_bytes(S, p) + (size_t)4 * p * sel_ngmax(p) * tile + (size_t)4 * p * tile;
 }
 
 template <int B>
@@ -414,7 +512,8 @@ cudaError_t launch_backward(int n, int k, int b, const double* L, long long ldl,
   const int S = (n + b - 1) / b;
   int p = (k + b - 1) / b;
   if (p > S - 1) p = S - 1;
-  cudaError_t e = cudaMemsetAsync(ws, 0, selinv_workspace_bytes(n, k, b), st);
+  const int pw = p < 1 ? 1 : p;   // scratch sizing (p = 0 has no off-diagonal tiles)
+  cudaError_t e = cudaMemsetAsync(ws, 0, 256 + sel_flag_bytes(S, pw), st);   // control + flags (not the scratch)
   if (e != cudaSuccess) return e;
   const long long nb0 = (long long)(k + 1) * n;
   zero_band_kernel<<<(unsigned)((nb0 + 255) / 256), 256, 0, st>>>(g, ldg, n, k);
@@ -430,8 +529,11 @@ cudaError_t launch_backward(int n, int k, int b, const double* L, long long ldl,
   a.S = S;
   a.p = p;
   a.total = sel_total(S, p);
+  a.ngmax = sel_ngmax(pw);
   a.ctl = reinterpret_cast<Control*>(ws);
   a.flags = reinterpret_cast<int*>(static_cast<char*>(ws) + 256);
+  a.part = reinterpret_cast<double*>(static_cast<char*>(ws) + 256 + sel_flag_bytes(S, pw));
+  a.wsh = a.part + (size_t)4 * pw * a.ngmax * b * b;
   a.status = status;
   a.wait_ns = wait_ns;
   switch (b) {
@@ -443,6 +545,21 @@ cudaError_t launch_backward(int n, int k, int b, const double* L, long long ldl,
   const long long nb = (long long)(k + 1) * n;
   grad_from_sigma_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(g, ldg, n, k, x, bbar, ldbar);
   return cudaGetLastError();
+}
+
+long long adjoint_plan_count(int n, int k, int b) {
+  const int S = (n + b - 1) / b;
+  int p = (k + b - 1) / b;
+  if (p > S - 1) p = S - 1;
+  if (n <= 0) return 0;
+  return (long long)sel_total(S, p);
+}
+
+void adjoint_plan_task(int n, int k, int b, long long t, int* type, int* J, int* I, int* g) {
+  const int S = (n + b - 1) / b;
+  int p = (k + b - 1) / b;
+  if (p > S - 1) p = S - 1;
+  sel_decode(S, p, t, *type, *J, *I, *g);
 }
 
 cudaError_t launch_logdet(const double* ab, long long ldab, int n, double* out, cudaStream_t st) {
