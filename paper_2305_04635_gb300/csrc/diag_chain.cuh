@@ -309,7 +309,10 @@ __device__ __forceinline__ void diag_syrk(DiagSmem<B, F32>& sm, const double* X,
 // shared memory; the recurrence's own entry D(j+1, j+1) is left out of column
 // j's update.  U is kept for the next step's TRSM.  (Posting the next pivot's
 // two entries ahead of the rest of the column was measured slower: the update
-// warps, not the recurrence, then set the pace.)
+// warps, not the recurrence, then set the pace.  So was forming the products
+// D(i, j) D(l, j) before 1/d_j arrives, with the entries kept in registers:
+// the product pass lengthened the update warps' step by more than the
+// DMUL it took off the path.)
 template <int B, bool F32>
 __device__ __forceinline__ void diag_potrf(DiagSmem<B, F32>& sm, double* D, int jmax, int tid) {
   const int warp = tid >> 5, lane = tid & 31;
@@ -319,7 +322,6 @@ __device__ __forceinline__ void diag_potrf(DiagSmem<B, F32>& sm, double* D, int 
     if (lane == 0) {
       const double d = D[0];
       if (jmax >= 2) sm.q[1] = D[1] * D[1];
-      if (!(d > 0.0)) sm.fail = 1;
       sm.d[0] = d;
       inv = pivot_rcp(d);
       sm.inv[0] = inv;
@@ -329,7 +331,6 @@ __device__ __forceinline__ void diag_potrf(DiagSmem<B, F32>& sm, double* D, int 
       if (j >= 1) bar_sync(kBarU + ((j - 1) & 1), 128);
       if (lane == 0) {
         const double d = fma(-sm.q[j + 1], inv, D[(j + 1) * B + j + 1]);
-        if (!(d > 0.0) && sm.fail == 0) sm.fail = j + 2;
         sm.d[j + 1] = d;
         inv = pivot_rcp(d);
         sm.inv[j + 1] = inv;
@@ -337,6 +338,15 @@ __device__ __forceinline__ void diag_potrf(DiagSmem<B, F32>& sm, double* D, int 
       bar_arrive(kBarP + ((j + 1) & 1), 128);
     }
     if (jmax >= 2) bar_sync(kBarU + ((jmax - 2) & 1), 128);
+    // The first pivot that is not positive, found once the recurrence is done:
+    // a bad pivot only spoils the columns after it, and the step is then
+    // abandoned, so the recurrence itself carries no test.
+    if (lane == 0) {
+      int f = 0;
+      for (int j = jmax - 1; j >= 0; --j)
+        if (!(sm.d[j] > 0.0)) f = j + 1;
+      sm.fail = f;
+    }
   } else {
     const int u = tid - 32;
     for (int j = 0; j < jmax; ++j) {
