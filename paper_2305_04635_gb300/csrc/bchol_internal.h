@@ -18,6 +18,9 @@ struct FactorPlan {
   long long Treg = 0;          // tasks per such block: 2p + 1 + p(p-1)/2
   long long Treg_cp = 0;       // tickets per such block with the diagonal chain: 2(p-1) + p(p-1)/2
   unsigned long long total_cp = 0;  // tickets with the diagonal chain (tiles of 16 and 32)
+  long long Treg_hp = 0;       // tickets per such block with the chain and two helper CTAs: 2(p-2) + p(p-1)/2 - 1
+  unsigned long long total_hp = 0;  // tickets with the chain and the helpers
+  bool helper = false;         // tiles of 16 and 32 with 2 <= p <= 40: the chain plus two helper CTAs
   unsigned long long total = 0;  // tasks of the whole factorization
   size_t flag_count = 0;       // ints of ready flags: S*(p+1)
   bool f32_update = false;     // mixed precision: trailing updates accumulated in FP32

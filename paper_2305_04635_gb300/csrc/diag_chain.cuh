@@ -338,14 +338,16 @@ __device__ __forceinline__ void diag_potrf(DiagSmem<B, F32>& sm, double* D, int 
       bar_arrive(kBarP + ((j + 1) & 1), 128);
     }
     if (jmax >= 2) bar_sync(kBarU + ((jmax - 2) & 1), 128);
-    // The first pivot that is not positive, found once the recurrence is done:
-    // a bad pivot only spoils the columns after it, and the step is then
-    // abandoned, so the recurrence itself carries no test.
-    if (lane == 0) {
-      int f = 0;
-      for (int j = jmax - 1; j >= 0; --j)
-        if (!(sm.d[j] > 0.0)) f = j + 1;
-      sm.fail = f;
+    // The first pivot that is not positive, found once the recurrence is done
+    // (one pivot per lane): a bad pivot only spoils the columns after it, and
+    // the step is then abandoned, so the recurrence itself carries no test.
+    for (int j0 = 0; j0 < jmax; j0 += 32) {
+      const unsigned bad = __ballot_sync(0xffffffffu, j0 + lane < jmax && !(sm.d[j0 + lane] > 0.0));
+      if (bad) {
+        if (lane == 0) sm.fail = j0 + __ffs(bad);
+        break;
+      }
+      if (lane == 0) sm.fail = 0;
     }
   } else {
     const int u = tid - 32;

@@ -26,10 +26,15 @@
 // With tiles of 16 or 32 the first CTA of the launch runs the diagonal chain
 // instead (diag_chain.cuh): every task of the diagonal and the first
 // sub-diagonal, fused per step, and the other CTAs take the rest by ticket in
-// the order of decode_cp_ticket.  All CTAs of the launch are resident at once
-// (the grid is sized from the occupancy), and every task the chain waits for
-// precedes, in the combined order, every ticket that waits for the chain, so
-// this walk cannot deadlock either.
+// the order of decode_cp_ticket.  When the band holds two or more tiles below
+// the diagonal, CTAs 1 and 2 are helpers that run the three tasks of each step
+// at distance two from the diagonal in a fixed order (the tasks the chain's
+// next inputs hang on, so that they never queue behind other tickets; two
+// CTAs, because one SM's FP64 rate does not fit the three into a chain step),
+// and the tickets follow decode_hp_ticket.  All CTAs of the launch are resident at
+// once (the grid is sized from the occupancy), and every task the chain or a
+// helper waits for precedes, in the combined order, every task that waits for
+// it, so this walk cannot deadlock either.
 #include <algorithm>
 #include <cstdio>
 
@@ -37,16 +42,49 @@
 
 namespace bchol {
 
-template <int B, bool F32, bool CP>
+template <int B, bool F32>
+__device__ __forceinline__ bool run_task(const FactorArgs& a, int type, int s, int I, int J, Smem<B>& sm, int* s_flag) {
+  if (type == kPotrf) return task_potrf<B>(a, s, sm, s_flag);
+  if (type == kTrsm && F32) return task_trsm_f32<B>(a, I, s, sm, s_flag);
+  if (type == kTrsm) return task_trsm<B>(a, I, s, sm, s_flag);
+  if (F32) return task_upd_f32<B>(a, I, J, s, sm, s_flag);
+  return task_upd<B>(a, I, J, s, sm, s_flag);
+}
+
+// Helper CTA `role` (1 or 2) of the chain mode with helpers: the tasks at
+// distance two from the diagonal, in step order (schedule.cuh).  Helper 1
+// solves L(t, t-2) and applies it to A(t, t); helper 2 applies it to A(t, t-1)
+// once the chain's L(t-1, t-2) is in.
+template <int B, bool F32>
+__device__ void factor_helper(const FactorArgs& a, Smem<B>& sm, int* s_flag, int role) {
+  for (int t = 2; t < a.S; ++t) {
+    bool ok;
+    if (role == 1)
+      ok = run_task<B, F32>(a, kTrsm, t - 2, t, t - 2, sm, s_flag) && run_task<B, F32>(a, kUpd, t - 2, t, t, sm, s_flag);
+    else
+      ok = run_task<B, F32>(a, kUpd, t - 2, t, t - 1, sm, s_flag);
+    if (!ok) return;
+  }
+}
+
+// MODE 0: tickets only; 1: the diagonal chain (CTA 0) and tickets; 2: the chain,
+// two helpers (CTAs 1 and 2) and tickets.
+template <int B, bool F32, int MODE>
 __global__ void __launch_bounds__(kThreads, 2) factor_kernel(FactorArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ long long s_task;
   __shared__ int s_flag;
-  if constexpr (CP) {
+  if constexpr (MODE >= 1) {
     if (blockIdx.x == 0) {
       if (threadIdx.x == 0) st_release(&a.ctl->chain_sm, sm_id() + 1);
       diag_chain<B, F32>(a, *reinterpret_cast<DiagSmem<B, F32>*>(smem_raw));
       return;
+    }
+    if constexpr (MODE == 2) {
+      if (blockIdx.x <= 2) {
+        factor_helper<B, F32>(a, *reinterpret_cast<Smem<B>*>(smem_raw), &s_flag, (int)blockIdx.x);
+        return;
+      }
     }
     // A ticket CTA on the chain CTA's SM leaves: the chain's FP64 work is the
     // critical path and each SM sub-partition's FP64 unit is shared.  (All CTAs
@@ -71,22 +109,13 @@ __global__ void __launch_bounds__(kThreads, 2) factor_kernel(FactorArgs a) {
     if (t >= (long long)a.total) break;
     if (threadIdx.x == 0) next = atomicAdd(&a.ctl->ticket, 1ULL);  // claim the next task early
     int type, s, I, J;
-    if constexpr (CP)
+    if constexpr (MODE == 2)
+      decode_hp_ticket(Schedule{a.S, a.p, a.Sreg, a.Treg}, t, type, s, I, J);
+    else if constexpr (MODE == 1)
       decode_cp_ticket(Schedule{a.S, a.p, a.Sreg, a.Treg}, t, type, s, I, J);
     else
       decode_task(Schedule{a.S, a.p, a.Sreg, a.Treg}, t, type, s, I, J);
-    bool ok;
-    if (type == kPotrf)
-      ok = task_potrf<B>(a, s, sm, &s_flag);
-    else if (type == kTrsm && F32)
-      ok = task_trsm_f32<B>(a, I, s, sm, &s_flag);
-    else if (type == kTrsm)
-      ok = task_trsm<B>(a, I, s, sm, &s_flag);
-    else if (F32)
-      ok = task_upd_f32<B>(a, I, J, s, sm, &s_flag);
-    else
-      ok = task_upd<B>(a, I, J, s, sm, &s_flag);
-    if (!ok) break;
+    if (!run_task<B, F32>(a, type, s, I, J, sm, &s_flag)) break;
   }
 }
 
@@ -124,28 +153,37 @@ FactorPlan make_factor_plan(int n, int k, int b) {
   tickets += (unsigned long long)P.Sreg * (unsigned long long)P.Treg_cp;
   for (int s = (int)P.Sreg; s < P.S; ++s) tickets += (unsigned long long)cp_block_size(cs, s);
   P.total_cp = tickets;
+  // Helpers pay off while the chain bounds the launch; with many tiles per
+  // panel (k = 2000 at b = 32) the two CTAs are worth more as ticket CTAs.
+  P.helper = (b <= 32 && P.p >= 2 && P.p <= 40);
+  P.Treg_hp = hp_treg(P.p);
+  const Schedule hs{P.S, P.p, P.Sreg, P.Treg_hp};
+  tickets = (unsigned long long)hp_panel0(hs);
+  tickets += (unsigned long long)P.Sreg * (unsigned long long)P.Treg_hp;
+  for (int s = (int)P.Sreg; s < P.S; ++s) tickets += (unsigned long long)hp_block_size(hs, s);
+  P.total_hp = tickets;
   return P;
 }
 
 size_t factor_workspace_bytes(const FactorPlan& P) { return 256 + P.flag_count * sizeof(int); }
 
-template <int B, bool F32, bool CP>
+template <int B, bool F32, int MODE>
 static cudaError_t launch_b(const FactorArgs& a, int ctas_per_sm, cudaStream_t stream) {
   size_t smem = sizeof(Smem<B>);
-  if constexpr (CP) smem = std::max(smem, sizeof(DiagSmem<B, F32>));
+  if constexpr (MODE >= 1) smem = std::max(smem, sizeof(DiagSmem<B, F32>));
   cudaError_t e =
-      cudaFuncSetAttribute(factor_kernel<B, F32, CP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(factor_kernel<B, F32, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, factor_kernel<B, F32, CP>, kThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, factor_kernel<B, F32, MODE>, kThreads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
   long long grid = (long long)per_sm * num_sms();
-  const unsigned long long need = a.total + (CP ? 1 : 0);  // tickets (+ the chain CTA)
+  const unsigned long long need = a.total + (MODE == 2 ? 3 : MODE == 1 ? 1 : 0);  // tickets + chain (+ helpers)
   if ((unsigned long long)grid > need) grid = (long long)need;
   if (grid < 1) grid = 1;
-  factor_kernel<B, F32, CP><<<(unsigned)grid, kThreads, smem, stream>>>(a);
+  factor_kernel<B, F32, MODE><<<(unsigned)grid, kThreads, smem, stream>>>(a);
   return cudaGetLastError();
 }
 
@@ -173,35 +211,42 @@ cudaError_t launch_factor(const FactorPlan& P, double* ab, long long ldab, int* 
   a.stall = -1;
   if (stall_I >= 0 && stall_J >= 0 && stall_I < P.S && stall_J <= stall_I && stall_I - stall_J <= P.p)
     a.stall = stall_J * (P.p + 1) + (stall_I - stall_J);
-  if (P.b <= 32) {  // diagonal chain + tickets
-    a.Treg = P.Treg_cp;
-    a.total = P.total_cp;
+  if (P.b <= 32) {  // diagonal chain (+ helpers) + tickets
+    a.Treg = P.helper ? P.Treg_hp : P.Treg_cp;
+    a.total = P.helper ? P.total_hp : P.total_cp;
   }
+  const bool h = P.helper;
   if (P.f32_update) {
     switch (P.b) {
-      case 16: return launch_b<16, true, true>(a, ctas_per_sm, stream);
-      case 32: return launch_b<32, true, true>(a, ctas_per_sm, stream);
-      case 64: return launch_b<64, true, false>(a, ctas_per_sm, stream);
+      case 16: return h ? launch_b<16, true, 2>(a, ctas_per_sm, stream) : launch_b<16, true, 1>(a, ctas_per_sm, stream);
+      case 32: return h ? launch_b<32, true, 2>(a, ctas_per_sm, stream) : launch_b<32, true, 1>(a, ctas_per_sm, stream);
+      case 64: return launch_b<64, true, 0>(a, ctas_per_sm, stream);
       default: return cudaErrorInvalidValue;
     }
   }
   switch (P.b) {
-    case 16: return launch_b<16, false, true>(a, ctas_per_sm, stream);
-    case 32: return launch_b<32, false, true>(a, ctas_per_sm, stream);
-    case 64: return launch_b<64, false, false>(a, ctas_per_sm, stream);
+    case 16: return h ? launch_b<16, false, 2>(a, ctas_per_sm, stream) : launch_b<16, false, 1>(a, ctas_per_sm, stream);
+    case 32: return h ? launch_b<32, false, 2>(a, ctas_per_sm, stream) : launch_b<32, false, 1>(a, ctas_per_sm, stream);
+    case 64: return launch_b<64, false, 0>(a, ctas_per_sm, stream);
     default: return cudaErrorInvalidValue;
   }
 }
 
 // The combined task order of one factorization (host side): for tiles of 16
-// and 32, the diagonal chain's tasks at their places among the tickets;
-// for 64, the ticket order itself.
+// and 32, the diagonal chain's (and the helpers') tasks at their places among
+// the tickets; for 64, the ticket order itself.
 void plan_task(const FactorPlan& P, long long t, int& type, int& s, int& I, int& J) {
   if (P.b > 32) {
     decode_task(Schedule{P.S, P.p, P.Sreg, P.Treg}, t, type, s, I, J);
     return;
   }
-  const Schedule cs{P.S, P.p, P.Sreg, P.Treg_cp};
+  const Schedule cs{P.S, P.p, P.Sreg, P.helper ? P.Treg_hp : P.Treg_cp};
+  auto ticket = [&](long long u) {
+    if (P.helper)
+      decode_hp_ticket(cs, u, type, s, I, J);
+    else
+      decode_cp_ticket(cs, u, type, s, I, J);
+  };
   const long long nd = P.p >= 1 ? 3 : 1;
   auto diag = [&](int st, long long r) {
     if (st == 0 || P.p == 0 || r == 2) {
@@ -222,9 +267,9 @@ void plan_task(const FactorPlan& P, long long t, int& type, int& s, int& I, int&
     return;
   }
   t -= 1;
-  long long base = cp_panel0(cs);
+  long long base = P.helper ? hp_panel0(cs) : cp_panel0(cs);
   if (t < base) {
-    decode_cp_ticket(cs, t, type, s, I, J);
+    ticket(t);
     return;
   }
   t -= base;
@@ -234,9 +279,19 @@ void plan_task(const FactorPlan& P, long long t, int& type, int& s, int& I, int&
       return;
     }
     t -= nd;
-    const long long bs = cp_block_size(cs, st);
+    if (P.helper && st + 2 < P.S) {  // H(st+2): TRSM(st+2, st), UPD(st+2, st+2, st), UPD(st+2, st+1, st)
+      if (t < 3) {
+        s = st;
+        I = st + 2;
+        type = t == 0 ? kTrsm : kUpd;
+        J = t == 0 ? st : t == 1 ? st + 2 : st + 1;
+        return;
+      }
+      t -= 3;
+    }
+    const long long bs = P.helper ? hp_block_size(cs, st) : cp_block_size(cs, st);
     if (t < bs) {
-      decode_cp_ticket(cs, base + t, type, s, I, J);
+      ticket(base + t);
       return;
     }
     t -= bs;

@@ -189,4 +189,107 @@ __host__ __device__ inline void decode_cp_ticket(const Schedule& a, long long t,
   }
 }
 
+// ----------------------------------------------------------------------------
+// Order with the diagonal chain and two helper CTAs (p >= 2).  The helpers run,
+// for t = 2, 3, ..., the three tasks at distance two from the diagonal that the
+// chain's next inputs hang on:
+//     helper 1:  TRSM(t, t-2), then UPD(t, t, t-2)     (L(t, t-2) and the last outside update of A(t, t))
+//     helper 2:  UPD(t, t-1, t-2)                      (the last outside update of A(t, t-1))
+// so they no longer queue behind other tickets.  The tickets are the chain
+// order's without them:
+//     panel''(s) TRSM(s+2+r, s),      r = 1..m_s-2
+//     near''(s)  UPD(s+2+r, s+1, s),  r = 1..m_s-2
+//     far'(s)    far(s) without UPD(s+2, s+2, s)
+// in blocks block''(s) = near''(s), panel''(s+1), far'(s) after panel''(0).
+// In the combined order
+//     DIAG(0), panel''(0), DIAG(1), H(2), block''(0), DIAG(2), H(3), block''(1), ...
+// (H(t) = the three helper tasks of t) every task comes after the tasks it
+// reads: H(t) reads DIAG(t-2), DIAG(t-1) and blocks up to t-3; block''(s)
+// reads H(s+2) (L(s+2, s)) and DIAG(s+1) at most; DIAG(s) reads H(s).
+// Regular blocks hold 2(p-2) + p(p-1)/2 - 1 tickets.
+
+__host__ __device__ inline long long hp_treg(int p) {
+  return p >= 2 ? 2LL * (p - 2) + (long long)p * (p - 1) / 2 - 1 : 0;
+}
+
+__host__ __device__ inline long long hp_panel0(const Schedule& a) {
+  const int m0 = sched_m(a, 0);
+  return m0 > 2 ? m0 - 2 : 0;
+}
+
+__host__ __device__ inline long long hp_block_size(const Schedule& a, int s) {
+  const long long ms = sched_m(a, s);
+  long long size = (ms > 2 ? ms - 2 : 0) + ms * (ms - 1) / 2 - (ms >= 2 ? 1 : 0);
+  if (s + 1 < a.S) {
+    const long long m1 = sched_m(a, s + 1);
+    size += m1 > 2 ? m1 - 2 : 0;
+  }
+  return size;
+}
+
+// Ticket t (0-based, tickets only) -> task.  `a.Treg` must be hp_treg(p).
+__host__ __device__ inline void decode_hp_ticket(const Schedule& a, long long t, int& type, int& s, int& I, int& J) {
+  const long long P0 = hp_panel0(a);
+  if (t < P0) {  // panel''(0)
+    type = kTrsm;
+    s = 0;
+    J = 0;
+    I = 3 + (int)t;
+    return;
+  }
+  t -= P0;
+  if (a.Treg > 0 && t < a.Sreg * a.Treg) {
+    s = (int)(t / a.Treg);
+    t -= (long long)s * a.Treg;
+  } else {
+    t -= a.Sreg * a.Treg;
+    s = (int)a.Sreg;
+    while (true) {
+      const long long size = hp_block_size(a, s);
+      if (t < size) break;
+      t -= size;
+      ++s;
+    }
+  }
+  const int ms = sched_m(a, s);
+  const long long nnear = ms > 2 ? ms - 2 : 0;
+  if (t < nnear) {  // near''(s)
+    type = kUpd;
+    J = s + 1;
+    I = s + 3 + (int)t;
+    return;
+  }
+  t -= nnear;
+  if (s + 1 < a.S) {  // panel''(s+1)
+    const int m1 = sched_m(a, s + 1);
+    const long long npan = m1 > 2 ? m1 - 2 : 0;
+    if (t < npan) {
+      type = kTrsm;
+      s = s + 1;
+      J = s;
+      I = s + 3 + (int)t;
+      return;
+    }
+    t -= npan;
+  }
+  type = kUpd;  // far'(s): column s+2 from row s+3, then columns s+3.. in full
+  J = s + 2;
+  const long long first = ms > 2 ? ms - 2 : 0;
+  if (t < first) {
+    I = s + 3 + (int)t;
+    return;
+  }
+  t -= first;
+  for (J = s + 3; J <= s + ms; ++J) {
+    const long long cnt = s + ms - J + 1;
+    if (t < cnt) {
+      I = J + (int)t;
+      return;
+    }
+    t -= cnt;
+  }
+  type = -1;  // past the last ticket
+  I = J = -1;
+}
+
 }  // namespace bchol

@@ -28,7 +28,7 @@ def expected_tasks(n, k, b):
 
 @pytest.mark.parametrize("n,k,b", [(1, 0, 16), (10, 3, 16), (100, 31, 32), (100, 32, 32), (129, 64, 64),
                                    (1000, 50, 16), (500, 0, 32), (50, 60, 16), (3000, 130, 32), (777, 200, 64),
-                                   (640, 639, 64)])
+                                   (640, 639, 64), (200, 20, 16), (40, 39, 16), (33, 32, 16), (48, 17, 16)])
 def test_schedule_is_complete_and_topological(n, k, b):
     got = bchol.plan_tasks(n, k, b)
     want, S, p = expected_tasks(n, k, b)
@@ -70,21 +70,37 @@ def _is_chain(task):
     return typ == 0 or (typ == 1 and I == s + 1) or (typ == 2 and I == J == s + 1)
 
 
+def _helper(task):
+    """Helper CTA (1 or 2) that runs a task when the band holds two or more tiles below the diagonal,
+    else 0: helper 1 runs TRSM(s+2, s) and UPD(s+2, s+2, s), helper 2 runs UPD(s+2, s+1, s)."""
+    typ, s, I, J = task
+    if I != s + 2:
+        return 0
+    if typ == 1 or (typ == 2 and J == I):
+        return 1
+    return 2 if typ == 2 and J == s + 1 else 0
+
+
 @pytest.mark.parametrize("workers", [1, 2, 5])
 @pytest.mark.parametrize("n,k,b", [(1000, 50, 16), (640, 200, 32), (777, 90, 16), (300, 16, 16), (100, 0, 16),
-                                   (129, 64, 64)])
+                                   (129, 64, 64), (200, 20, 16), (40, 39, 16), (33, 32, 16)])
 def test_launch_cannot_deadlock(n, k, b, workers):
-    """Simulate the persistent launch: the chain CTA runs its tasks in order; each ticket CTA claims
-    the next ticket, and claims one more before it starts the one it holds (as the kernel does).
-    A task runs once every task it reads is done.  Progress must never stop."""
+    """Simulate the persistent launch: the chain CTA and the two helper CTAs run their tasks in
+    order; each ticket CTA claims the next ticket, and claims one more before it starts the one
+    it holds (as the kernel does).  A task runs once every task it reads is done.  Progress must
+    never stop."""
     order = bchol.plan_tasks(n, k, b)
     kk = min(k, n - 1)
     S = math.ceil(n / b)
     p = min(math.ceil(kk / b), S - 1)
     chain_mode = b <= 32
+    helpers = chain_mode and p >= 2
     chain = [t for t in order if chain_mode and _is_chain(t)]
-    tickets = [t for t in order if not (chain_mode and _is_chain(t))]
+    agents = [[t for t in order if helpers and _helper(t) == r] for r in (1, 2)]
+    tickets = [t for t in order if not (chain_mode and _is_chain(t)) and not (helpers and _helper(t))]
+    assert len(chain) + sum(map(len, agents)) + len(tickets) == len(order)
     done = set()
+    ai = [0, 0]
     ci, next_ticket = 0, 0
     held = [[] for _ in range(workers)]
     while len(done) < len(order):
@@ -100,4 +116,9 @@ def test_launch_cannot_deadlock(n, k, b, workers):
             done.add(chain[ci])
             ci += 1
             progress = True
+        for r in range(2):
+            if ai[r] < len(agents[r]) and all(d in done for d in _deps(agents[r][ai[r]], p)):
+                done.add(agents[r][ai[r]])
+                ai[r] += 1
+                progress = True
         assert progress, f"stalled with {len(done)} of {len(order)} tasks done"
