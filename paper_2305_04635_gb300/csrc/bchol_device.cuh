@@ -83,6 +83,34 @@ __device__ __forceinline__ void load_tile(const double* __restrict__ ab, long lo
   }
 }
 
+// Element idx (column-major: i = idx % B, j = idx / B) of band tile (I,J), as load_tile reads it.
+__device__ __forceinline__ double tile_elem(const double* __restrict__ ab, long long ldab, int n, int k, int I, int J,
+                                            int idx, int B) {
+  const int i = idx % B, j = idx / B;
+  const int gi = I * B + i, gj = J * B + j;
+  const int d = gi - gj;
+  return (gi < n && gj < n && d >= 0 && d <= k) ? __ldcg(ab + d + (long long)gj * ldab) : 0.0;
+}
+
+// Two band tiles at once (every load of both is issued before any store).
+template <int B, int NT>
+__device__ __forceinline__ void load_tile2(const double* __restrict__ ab, long long ldab, int n, int k, int I1, int J1,
+                                           double* s1, int I2, int J2, double* s2) {
+  static_assert((B * B) % NT == 0, "whole passes");
+  constexpr int E = B * B / NT;
+  double v1[E], v2[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    v1[e] = tile_elem(ab, ldab, n, k, I1, J1, threadIdx.x + e * NT, B);
+    v2[e] = tile_elem(ab, ldab, n, k, I2, J2, threadIdx.x + e * NT, B);
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    s1[threadIdx.x + e * NT] = v1[e];
+    s2[threadIdx.x + e * NT] = v2[e];
+  }
+}
+
 // Store the in-band, in-matrix elements of a column-major shared tile.
 template <int B, int NT>
 __device__ __forceinline__ void store_tile(double* __restrict__ ab, long long ldab, int n, int k, int I, int J,

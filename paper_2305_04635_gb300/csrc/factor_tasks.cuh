@@ -122,8 +122,9 @@ __device__ bool task_potrf(const FactorArgs& a, int s, Smem<B>& sm, int* s_flag)
 
 // ---------------------------------------------------------------- TRSM(I,s)
 // X = A_Is L_ss^{-T}, row by row: TPR threads own a row, thread `sub` keeps
-// the columns l = sub (mod TPR) in registers; column j's value is formed by
-// its owner and shuffled to the row group.  No block barriers in the loop.
+// the columns l = sub (mod TPR) in registers; column j's value, final when the
+// sweep reaches it, is shuffled to the row group.  No block barriers in the
+// loop, and no division or scaling on its chain (the unit lower form below).
 template <int B>
 __device__ bool task_trsm(const FactorArgs& a, int I, int s, Smem<B>& sm, int* s_flag) {
   constexpr int TPR = kThreads / B;
@@ -139,33 +140,35 @@ __device__ bool task_trsm(const FactorArgs& a, int I, int s, Smem<B>& sm, int* s
   if (!*s_flag) return false;
   double* sX = sm.t0;
   double* sL = sm.t1;
-  load_tile<B, kThreads>(a.ab, a.ldab, a.n, a.k, I, s, sX);
-  load_tile<B, kThreads>(a.ab, a.ldab, a.n, a.k, s, s, sL);
+  load_tile2<B, kThreads>(a.ab, a.ldab, a.n, a.k, I, s, sX, s, s, sL);
   __syncthreads();
   const int jmax = min(B, a.n - s * B);
   if (tid < B) s_rinv[tid] = (tid < jmax) ? 1.0 / sL[tid * B + tid] : 0.0;
+  __syncthreads();
+  // X L^T = A with L = U diag(L_jj), U unit lower: the rows of Z = X diag(L_jj)
+  // solve Z U^T = A, one shuffle and one DFMA per step (no scaling on the
+  // chain), and X = Z diag(1 / L_jj) at the end.
+  for (int idx = tid; idx < B * B; idx += kThreads) {
+    const int l = idx % B, j = idx / B;
+    if (l > j) sL[idx] *= s_rinv[j];
+  }
   const int i = tid / TPR, sub = tid % TPR;
   double acc[R];
 #pragma unroll
   for (int q = 0; q < R; ++q) acc[q] = sX[(sub + q * TPR) * B + i];
   __syncthreads();
 #pragma unroll
-  for (int j = 0; j < B; ++j) {
+  for (int j = 0; j < B - 1; ++j) {
     const int owner = j % TPR, qj = j / TPR;
-    double x = 0.0;
-    if (sub == owner) {
-      x = acc[qj] * s_rinv[j];
-      acc[qj] = x;
-    }
-    x = __shfl_sync(0xffffffffu, x, owner, TPR);
+    const double z = __shfl_sync(0xffffffffu, acc[qj], owner, TPR);
 #pragma unroll
     for (int q = qj; q < R; ++q) {
       const int l = sub + q * TPR;
-      if (l > j) acc[q] = fma(-x, sL[j * B + l], acc[q]);
+      if (l > j) acc[q] = fma(-z, sL[j * B + l], acc[q]);
     }
   }
 #pragma unroll
-  for (int q = 0; q < R; ++q) sX[(sub + q * TPR) * B + i] = acc[q];
+  for (int q = 0; q < R; ++q) sX[(sub + q * TPR) * B + i] = acc[q] * s_rinv[sub + q * TPR];
   __syncthreads();
   store_tile<B, kThreads>(a.ab, a.ldab, a.n, a.k, I, s, sX);
   publish(&a.flags[fidx(a, I, s)], s - first_step(a, I) + 1);
@@ -194,7 +197,12 @@ __device__ bool task_upd(const FactorArgs& a, int I, int J, int s, Smem<B>& sm, 
   if (!*s_flag) return false;
   double* sA = sm.t0;
   double* sB = sm.t1;
-  load_tile<B, kThreads>(a.ab, a.ldab, a.n, a.k, I, s, sA);
+  // Both L tiles go through registers and reach shared memory together, so
+  // that the loads of L_Is are still in flight while L_Js is waited for.
+  constexpr int E = B * B / kThreads;
+  double li[E], lj[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) li[e] = tile_elem(a.ab, a.ldab, a.n, a.k, I, s, tid + e * kThreads, B);
   const int ty = tid / 16, tx = tid % 16;
   const bool diag = (I == J);
   double acc[R][R];
@@ -211,7 +219,14 @@ __device__ bool task_upd(const FactorArgs& a, int I, int J, int s, Smem<B>& sm, 
     if (tid == 0) s_ok_j = wait_tile(a, J, s, s - first_step(a, J) + 1);
     __syncthreads();
     if (!s_ok_j) return false;
-    load_tile<B, kThreads>(a.ab, a.ldab, a.n, a.k, J, s, sB);
+#pragma unroll
+    for (int e = 0; e < E; ++e) lj[e] = tile_elem(a.ab, a.ldab, a.n, a.k, J, s, tid + e * kThreads, B);
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int idx = tid + e * kThreads;
+    sA[idx] = li[e];
+    if (J != I) sB[idx] = lj[e];
   }
   const double* sBr = (J != I) ? sB : sA;
   __syncthreads();
