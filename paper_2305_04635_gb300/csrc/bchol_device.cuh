@@ -40,6 +40,7 @@ struct Control {
   int abort;                  // != 0: stop (a pivot failed or a wait ran out)
   int chain_sm;               // 1 + the SM of the diagonal-chain CTA, 0 until it is known
   int retired;                // batched launch: every ticket of this matrix is taken
+  int helper_sm[2];           // 1 + the SMs of the two helper CTAs, 0 until known (or without helpers)
   int pad;
 };
 

@@ -82,19 +82,29 @@ __global__ void __launch_bounds__(kThreads, 2) factor_kernel(FactorArgs a) {
     }
     if constexpr (MODE == 2) {
       if (blockIdx.x <= 2) {
+        if (threadIdx.x == 0) st_release(&a.ctl->helper_sm[blockIdx.x - 1], sm_id() + 1);
         factor_helper<B, F32>(a, *reinterpret_cast<Smem<B>*>(smem_raw), &s_flag, (int)blockIdx.x);
         return;
       }
     }
-    // A ticket CTA on the chain CTA's SM leaves: the chain's FP64 work is the
-    // critical path and each SM sub-partition's FP64 unit is shared.  (All CTAs
-    // are resident at once, so the chain CTA publishes its SM promptly; the
-    // wait is bounded and a CTA that gives up simply stays.)
+    // A ticket CTA on the SM of the chain CTA (or of a helper) leaves: their
+    // FP64 work is the critical path and each SM sub-partition's FP64 unit is
+    // shared.  (All CTAs are resident at once, so those CTAs publish their SMs
+    // promptly; the wait is bounded and a CTA that gives up simply stays.)
     if (threadIdx.x == 0) {
-      int c = ld_acquire(&a.ctl->chain_sm);
+      const int me = sm_id() + 1;
       const uint64_t t0 = globaltimer_ns();
+      int c = ld_acquire(&a.ctl->chain_sm);
       while (c == 0 && globaltimer_ns() - t0 < 200000ull) c = ld_acquire(&a.ctl->chain_sm);
-      s_flag = (c == sm_id() + 1);
+      bool leave = (c == me);
+      if constexpr (MODE == 2) {
+        for (int h = 0; h < 2 && !leave; ++h) {
+          int hs = ld_acquire(&a.ctl->helper_sm[h]);
+          while (hs == 0 && globaltimer_ns() - t0 < 200000ull) hs = ld_acquire(&a.ctl->helper_sm[h]);
+          leave = (hs == me);
+        }
+      }
+      s_flag = leave;
     }
     __syncthreads();
     if (s_flag) return;
