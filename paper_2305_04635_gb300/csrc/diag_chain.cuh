@@ -88,8 +88,7 @@ struct DiagSmem {
   int stop;       // any role: stop now
   int fail;       // POTRF: first non-positive pivot (1-based column in the tile), or 0
   int ok;         // compute: broadcast of a wait result
-  int pf_ok_d;    // prefetch: broadcast of the wait for A(s, s)
-  int pf_ok_x;    // prefetch: broadcast of the wait for A(s, s-1)
+  int pf_ok_d;    // prefetch: broadcast of the wait for A(s, s) and A(s, s-1)
 };
 
 constexpr unsigned kPollNs = 64;  // back-off of the service warps' polls
@@ -131,13 +130,29 @@ __device__ __forceinline__ bool wait_tile_poll(const FactorArgs& a, int I, int J
   }
 }
 
+// Tiles A(s, s) and A(s, s-1) together (96 threads): every load of both is in
+// flight before the first store into shared memory.
 template <int B>
-__device__ __forceinline__ void load_tile_group(const FactorArgs& a, int I, int J, double* s, int pt) {
-#pragma unroll 4
-  for (int idx = pt; idx < B * B; idx += 96) {
+__device__ __forceinline__ void load_tiles_group(const FactorArgs& a, int s, double* D, double* X, bool has_x,
+                                                 int pt) {
+  constexpr int E = (B * B + 95) / 96;
+  double vd[E], vx[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int idx = pt + 96 * e;
     const int i = idx % B, j = idx / B;
-    const int gi = I * B + i, gj = J * B + j, d = gi - gj;
-    s[j * B + i] = (gi < a.n && d >= 0 && d <= a.k) ? __ldcg(a.ab + d + (long long)gj * a.ldab) : 0.0;
+    const int gi = s * B + i, gd = s * B + j, gx = (s - 1) * B + j;
+    const bool in = idx < B * B && gi < a.n;
+    vd[e] = (in && gi - gd >= 0 && gi - gd <= a.k) ? __ldcg(a.ab + (gi - gd) + (long long)gd * a.ldab) : 0.0;
+    vx[e] = (has_x && in && gi - gx <= a.k) ? __ldcg(a.ab + (gi - gx) + (long long)gx * a.ldab) : 0.0;
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int idx = pt + 96 * e;
+    if (idx < B * B) {
+      D[idx] = vd[e];
+      if (has_x) X[idx] = vx[e];
+    }
   }
 }
 
@@ -175,9 +190,9 @@ __device__ void diag_publisher(const FactorArgs& a, DiagSmem<B, F32>& sm, int la
 // ------------------------------------------------------- prefetcher (warps 5-7)
 // For step s: waits until the other CTAs have applied every update of A(s, s)
 // and A(s, s-1) except the step s-1 DSYRK (steps s0(s) .. s-2), and copies both
-// tiles into buffer s & 1 (free once step s-2 is finished).  A(s, s) is usually
-// ready first: its last outside update comes a step earlier.  One thread
-// waits; the three warps copy.
+// tiles into buffer s & 1 (free once step s-2 is finished).  One thread waits
+// for both (A(s, s-1) is the later one); the three warps copy both tiles with
+// all loads in flight at once.
 template <int B, bool F32>
 __device__ void diag_prefetcher(const FactorArgs& a, DiagSmem<B, F32>& sm, int pt) {
   const uint64_t limit = 4 * a.wait_ns;
@@ -190,6 +205,7 @@ __device__ void diag_prefetcher(const FactorArgs& a, DiagSmem<B, F32>& sm, int p
       int ok = 1;
       if (s >= 2) ok = wait_smem_geq(&sm.consumed, s - 1, &sm.stop, a.ctl, a.status, limit);
       if (ok) ok = wait_tile_poll(a, s, s, has_x ? s - 1 - s0 : s - s0);
+      if (ok && has_x) ok = wait_tile_poll(a, s, s - 1, s - 1 - s0);
       sm.pf_ok_d = ok;
     }
     bar_sync(kBarPF, 96);
@@ -197,16 +213,7 @@ __device__ void diag_prefetcher(const FactorArgs& a, DiagSmem<B, F32>& sm, int p
       failed = true;
       break;
     }
-    load_tile_group<B>(a, s, s, sm.D[cur], pt);
-    if (has_x) {
-      if (pt == 0) sm.pf_ok_x = wait_tile_poll(a, s, s - 1, s - 1 - s0);
-      bar_sync(kBarPF, 96);
-      if (!sm.pf_ok_x) {
-        failed = true;
-        break;
-      }
-      load_tile_group<B>(a, s, s - 1, sm.X[cur], pt);
-    }
+    load_tiles_group<B>(a, s, sm.D[cur], sm.X[cur], has_x, pt);
     bar_sync(kBarPF, 96);
     if (pt == 0) st_release_cta(&sm.in_ready, s + 1);
   }

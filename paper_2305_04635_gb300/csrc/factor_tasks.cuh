@@ -322,11 +322,13 @@ __device__ bool task_trsm_f32(const FactorArgs& a, int I, int s, Smem<B>& sm, in
 template <int B>
 __device__ bool task_upd_f32(const FactorArgs& a, int I, int J, int s, Smem<B>& sm, int* s_flag) {
   constexpr int R = B / 16;
+  constexpr int E = B * B / kThreads;
   const int tid = threadIdx.x;
   const int s0I = first_step(a, I);
+  // As in task_upd: L_Is and A_IJ first, with their loads in flight while
+  // L_Js is waited for; A_IJ goes straight to registers.
   if (tid == 0) {
     bool ok = wait_tile(a, I, s, s - s0I + 1);
-    if (ok && J != I) ok = wait_tile(a, J, s, s - first_step(a, J) + 1);
     if (ok) ok = wait_tile(a, I, J, s - s0I);
     *s_flag = ok;
   }
@@ -334,20 +336,35 @@ __device__ bool task_upd_f32(const FactorArgs& a, int I, int J, int s, Smem<B>& 
   if (!*s_flag) return false;
   float* fA = reinterpret_cast<float*>(sm.t0);
   float* fB = reinterpret_cast<float*>(sm.t1);
-  for (int idx = tid; idx < B * B; idx += kThreads) {
-    const int i = idx % B, l = idx / B;
-    const int gl = s * B + l;
-    int gi = I * B + i, d = gi - gl;
-    fA[l * B + i] = (gi < a.n && d >= 0 && d <= a.k) ? (float)__ldcg(a.ab + d + (long long)gl * a.ldab) : 0.0f;
-    if (J != I) {
-      gi = J * B + i;
-      d = gi - gl;
-      fB[l * B + i] = (gi < a.n && d >= 0 && d <= a.k) ? (float)__ldcg(a.ab + d + (long long)gl * a.ldab) : 0.0f;
-    }
-  }
-  const float* fBr = (J != I) ? fB : fA;
+  double li[E], lj[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) li[e] = tile_elem(a.ab, a.ldab, a.n, a.k, I, s, tid + e * kThreads, B);
   const int ty = tid / 16, tx = tid % 16;
   const bool diag = (I == J);
+  double aij[R][R];
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int c = 0; c < R; ++c) {
+      const int gi = I * B + ty + 16 * r, gj = J * B + tx + 16 * c;
+      const int d = gi - gj;
+      aij[r][c] = (gi < a.n && d >= 0 && d <= a.k) ? __ldcg(a.ab + d + (long long)gj * a.ldab) : 0.0;
+    }
+  if (J != I) {
+    __shared__ int s_ok_j32;  // not s_flag: other threads may still be reading that one
+    if (tid == 0) s_ok_j32 = wait_tile(a, J, s, s - first_step(a, J) + 1);
+    __syncthreads();
+    if (!s_ok_j32) return false;
+#pragma unroll
+    for (int e = 0; e < E; ++e) lj[e] = tile_elem(a.ab, a.ldab, a.n, a.k, J, s, tid + e * kThreads, B);
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int idx = tid + e * kThreads;
+    fA[idx] = (float)li[e];
+    if (J != I) fB[idx] = (float)lj[e];
+  }
+  const float* fBr = (J != I) ? fB : fA;
   float acc[R][R];
 #pragma unroll
   for (int r = 0; r < R; ++r)
@@ -373,10 +390,7 @@ __device__ bool task_upd_f32(const FactorArgs& a, int I, int J, int s, Smem<B>& 
     for (int c = 0; c < R; ++c) {
       const int gi = I * B + ty + 16 * r, gj = J * B + tx + 16 * c;
       const int d = gi - gj;
-      if (gi < a.n && d >= 0 && d <= a.k) {
-        double* p = a.ab + d + (long long)gj * a.ldab;
-        *p = __ldcg(p) - (double)acc[r][c];
-      }
+      if (gi < a.n && d >= 0 && d <= a.k) a.ab[d + (long long)gj * a.ldab] = aij[r][c] - (double)acc[r][c];
     }
   publish(&a.flags[fidx(a, I, J)], s - s0I + 1);
   return true;
