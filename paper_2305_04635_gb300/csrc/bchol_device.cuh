@@ -41,7 +41,6 @@ struct Control {
   int chain_sm;               // 1 + the SM of the diagonal-chain CTA, 0 until it is known
   int retired;                // batched launch: every ticket of this matrix is taken
   int helper_sm[2];           // 1 + the SMs of the two helper CTAs, 0 until known (or without helpers)
-  int pad;
 };
 
 __device__ __forceinline__ int sm_id() {
