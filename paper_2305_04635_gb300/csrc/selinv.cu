@@ -263,6 +263,16 @@ __device__ bool sel_near(const SelArgs& a, int I, int J, Smem<B>& sm, int* s_fla
   if (!*s_flag) return false;
   double* sX = sm.t0;
   double* sY = sm.t1;
+  // L_JJ and L_IJ (final: the factor is done) are read now, into registers,
+  // so that their loads overlap the first product instead of following it
+  constexpr int E = B * B / kThreads;
+  double rjj[E], rij[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int idx = tid + e * kThreads, l = idx % B, j = idx / B;
+    rjj[e] = bget(a.L, a.ldl, a.n, a.k, J * B + l, J * B + j, false);   // -> sY[j*B + l]
+    rij[e] = bget(a.L, a.ldl, a.n, a.k, I * B + l, J * B + j, false);   // -> sY[l*B + j]
+  }
   for (int idx = tid; idx < B * B; idx += kThreads) {
     const int i = idx % B, l = idx / B;
     sX[l * B + i] = sget(a, I * B + i, (J + 1) * B + l);   // Sigma_{I,J+1} (symmetric when I = J+1)
@@ -285,35 +295,40 @@ __device__ bool sel_near(const SelArgs& a, int I, int J, Smem<B>& sm, int* s_fla
 #pragma unroll
     for (int c = 0; c < R; ++c) sP[(tx + 16 * c) * B + ty + 16 * r] = acc[r][c];
   __syncthreads();
-  for (int idx = tid; idx < B * B; idx += kThreads) {
-    const int l = idx % B, j = idx / B;
-    sY[j * B + l] = bget(a.L, a.ldl, a.n, a.k, J * B + l, J * B + j, false);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int idx = tid + e * kThreads;
+    sY[(idx / B) * B + idx % B] = rjj[e];
   }
   __syncthreads();
-  // Sigma_IJ = -P L_JJ^{-1}, row by row: back substitution over the columns, right to left
+  // Sigma_IJ = -P L_JJ^{-1}, row by row: back substitution over the columns,
+  // right to left, on the rows of L_JJ scaled by 1 / L_jj (no division or
+  // scaling on the chain; the result is scaled at the end)
   const int jmax = min(B, a.n - J * B);
   if (tid < B) s_rinv[tid] = (tid < jmax) ? 1.0 / sY[tid * B + tid] : 0.0;
+  __syncthreads();
+  for (int idx = tid; idx < B * B; idx += kThreads) {
+    const int j = idx % B, l = idx / B;
+    if (j > l) sY[idx] *= s_rinv[j];   // sY[l*B + j] = L(j, l) / L(j, j)
+  }
   const int i = tid / TPR, sub = tid % TPR;
   double sacc[RS];
 #pragma unroll
   for (int qq = 0; qq < RS; ++qq) sacc[qq] = -sP[(sub + qq * TPR) * B + i];
   __syncthreads();
 #pragma unroll
-  for (int jj = 0; jj < B; ++jj) {
+  for (int jj = 0; jj < B - 1; ++jj) {
     const int j = B - 1 - jj;
     const int owner = j % TPR, qj = j / TPR;
-    double x = 0.0;
-    if (sub == owner) {
-      x = sacc[qj] * s_rinv[j];
-      sacc[qj] = x;
-    }
-    x = __shfl_sync(0xffffffffu, x, owner, TPR);
+    const double z = __shfl_sync(0xffffffffu, sacc[qj], owner, TPR);
 #pragma unroll
     for (int qq = 0; qq <= qj; ++qq) {
       const int l = sub + qq * TPR;
-      if (l < j) sacc[qq] = fma(-x, sY[l * B + j], sacc[qq]);   // L(j, l)
+      if (l < j) sacc[qq] = fma(-z, sY[l * B + j], sacc[qq]);
     }
   }
+#pragma unroll
+  for (int qq = 0; qq < RS; ++qq) sacc[qq] *= s_rinv[sub + qq * TPR];
   __syncthreads();   // every warp is done with L_JJ in sY before it is overwritten below
   // store Sigma_IJ (band slots only) and keep the stored values (zero off the band) for the share
 #pragma unroll
@@ -323,9 +338,10 @@ __device__ bool sel_near(const SelArgs& a, int I, int J, Smem<B>& sm, int* s_fla
     if (in) a.sig[d + (long long)gj * a.lds] = sacc[qq];
     sX[i * B + sub + qq * TPR] = in ? sacc[qq] : 0.0;   // sX[l*B + c] = Sigma_IJ(l, c)
   }
-  for (int idx = tid; idx < B * B; idx += kThreads) {
-    const int l = idx % B, j = idx / B;
-    sY[l * B + j] = bget(a.L, a.ldl, a.n, a.k, I * B + l, J * B + j, false);   // sY[l*B + j] = L_IJ(l, j)
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int idx = tid + e * kThreads;
+    sY[(idx % B) * B + idx / B] = rij[e];   // sY[l*B + j] = L_IJ(l, j)
   }
   __syncthreads();
   // share(c, j) = sum_l Sigma_IJ(l, c) L_IJ(l, j), lower triangle c >= j
@@ -354,7 +370,7 @@ __device__ bool sel_near(const SelArgs& a, int I, int J, Smem<B>& sm, int* s_fla
 template <int B>
 __device__ bool sel_diag(const SelArgs& a, int J, Smem<B>& sm, int* s_flag) {
   __shared__ double sE[B * B];
-  __shared__ double s_part[B];
+  __shared__ double s_rl[B];
   const int tid = threadIdx.x;
   const int m = sel_m(a.S, a.p, J);
   if (tid == 0) *s_flag = wait_flag_geq(w_flag(a, J), m, a.ctl, a.status, a.wait_ns);
@@ -373,27 +389,30 @@ __device__ bool sel_diag(const SelArgs& a, int J, Smem<B>& sm, int* s_flag) {
   }
   __syncthreads();
   const int jmax = min(B, a.n - J * B);
-  for (int j = jmax - 1; j >= 0; --j) {
-    const double rl = 1.0 / sL[j * B + j];
-    // Sigma_ij for i > j (one thread per row)
-    if (tid < B && tid > j && tid < jmax) {
-      const int i = tid;
-      double s = sE[j * B + i];
-      for (int mm = j + 1; mm < jmax; ++mm) s = fma(sL[j * B + mm], sS[mm * B + i], s);   // L(mm,j) Sigma(i,mm)
-      const double v = -s * rl;
-      sS[j * B + i] = v;
-      s_part[i] = sL[j * B + i] * v;   // L(i,j) Sigma(i,j)
+  if (tid < B) s_rl[tid] = (tid < jmax) ? 1.0 / sL[tid * B + tid] : 0.0;   // every reciprocal at once
+  __syncthreads();
+  // The recurrence is warp 0's alone (row i on lane i), so warp barriers order
+  // it; the other warps wait at the block barrier below.
+  if (tid < 32) {
+    const int lane = tid;
+    for (int j = jmax - 1; j >= 0; --j) {
+      const double rl = s_rl[j];
+      double part = 0.0;
+      if (lane > j && lane < jmax) {   // Sigma_ij for i > j
+        double s = sE[j * B + lane];
+        for (int mm = j + 1; mm < jmax; ++mm) s = fma(sL[j * B + mm], sS[mm * B + lane], s);   // L(mm,j) Sigma(i,mm)
+        const double v = -s * rl;
+        sS[j * B + lane] = v;
+        part = sL[j * B + lane] * v;   // L(i,j) Sigma(i,j)
+      }
+#pragma unroll
+      for (int off = 16; off >= 1; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+      if (lane == 0) sS[j * B + j] = (rl - (sE[j * B + j] + part)) * rl;
+      if (lane > j && lane < jmax) sS[lane * B + j] = sS[j * B + lane];   // symmetric copy (row j)
+      __syncwarp();
     }
-    __syncthreads();
-    if (tid == 0) {
-      double t = sE[j * B + j];
-      for (int i = j + 1; i < jmax; ++i) t += s_part[i];
-      sS[j * B + j] = (rl - t) * rl;
-    }
-    __syncthreads();
-    if (tid < B && tid > j && tid < jmax) sS[tid * B + j] = sS[j * B + tid];   // symmetric copy (row j)
-    __syncthreads();
   }
+  __syncthreads();
   for (int idx = tid; idx < B * B; idx += kThreads) {
     const int i = idx % B, j = idx / B;
     if (i >= j && i < jmax) sput(a, J * B + i, J * B + j, sS[j * B + i]);
