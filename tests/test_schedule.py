@@ -28,7 +28,8 @@ def expected_tasks(n, k, b):
 
 @pytest.mark.parametrize("n,k,b", [(1, 0, 16), (10, 3, 16), (100, 31, 32), (100, 32, 32), (129, 64, 64),
                                    (1000, 50, 16), (500, 0, 32), (50, 60, 16), (3000, 130, 32), (777, 200, 64),
-                                   (640, 639, 64), (200, 20, 16), (40, 39, 16), (33, 32, 16), (48, 17, 16)])
+                                   (640, 639, 64), (200, 20, 16), (40, 39, 16), (33, 32, 16), (48, 17, 16),
+                                   (800, 640, 16), (800, 641, 16), (900, 700, 16)])
 def test_schedule_is_complete_and_topological(n, k, b):
     got = bchol.plan_tasks(n, k, b)
     want, S, p = expected_tasks(n, k, b)
@@ -83,7 +84,8 @@ def _helper(task):
 
 @pytest.mark.parametrize("workers", [1, 2, 5])
 @pytest.mark.parametrize("n,k,b", [(1000, 50, 16), (640, 200, 32), (777, 90, 16), (300, 16, 16), (100, 0, 16),
-                                   (129, 64, 64), (200, 20, 16), (40, 39, 16), (33, 32, 16)])
+                                   (129, 64, 64), (200, 20, 16), (40, 39, 16), (33, 32, 16), (800, 640, 16),
+                                   (800, 641, 16)])
 def test_launch_cannot_deadlock(n, k, b, workers):
     """Simulate the persistent launch: the chain CTA and the two helper CTAs run their tasks in
     order; each ticket CTA claims the next ticket, and claims one more before it starts the one
@@ -94,7 +96,7 @@ def test_launch_cannot_deadlock(n, k, b, workers):
     S = math.ceil(n / b)
     p = min(math.ceil(kk / b), S - 1)
     chain_mode = b <= 32
-    helpers = chain_mode and p >= 2
+    helpers = chain_mode and 2 <= p <= 40   # the launch runs helper CTAs in this range only
     chain = [t for t in order if chain_mode and _is_chain(t)]
     agents = [[t for t in order if helpers and _helper(t) == r] for r in (1, 2)]
     tickets = [t for t in order if not (chain_mode and _is_chain(t)) and not (helpers and _helper(t))]
