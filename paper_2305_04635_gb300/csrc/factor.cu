@@ -52,17 +52,22 @@ __device__ __forceinline__ bool run_task(const FactorArgs& a, int type, int s, i
 }
 
 // Helper CTA `role` (1 or 2) of the chain mode with helpers: the tasks at
-// distance two from the diagonal, in step order (schedule.cuh).  Helper 1
-// solves L(t, t-2) and applies it to A(t, t); helper 2 applies it to A(t, t-1)
-// once the chain's L(t-1, t-2) is in.
+// distance two from the diagonal, in step order (schedule.cuh).  Helper 2
+// solves L(t, t-2) and applies it to A(t, t-1) once the chain's L(t-1, t-2) is
+// in (A(t, t-1) is the chain's later input), using the solved tile straight
+// from its shared memory; helper 1 applies L(t, t-2) to A(t, t).
 template <int B, bool F32>
 __device__ void factor_helper(const FactorArgs& a, Smem<B>& sm, int* s_flag, int role) {
   for (int t = 2; t < a.S; ++t) {
     bool ok;
-    if (role == 1)
-      ok = run_task<B, F32>(a, kTrsm, t - 2, t, t - 2, sm, s_flag) && run_task<B, F32>(a, kUpd, t - 2, t, t, sm, s_flag);
-    else
-      ok = run_task<B, F32>(a, kUpd, t - 2, t, t - 1, sm, s_flag);
+    if (role == 1) {
+      ok = run_task<B, F32>(a, kUpd, t - 2, t, t, sm, s_flag);
+    } else if constexpr (F32) {
+      ok = run_task<B, F32>(a, kTrsm, t - 2, t, t - 2, sm, s_flag) &&
+           run_task<B, F32>(a, kUpd, t - 2, t, t - 1, sm, s_flag);
+    } else {
+      ok = task_trsm<B>(a, t, t - 2, sm, s_flag) && task_upd<B>(a, t, t - 1, t - 2, sm, s_flag, true);
+    }
     if (!ok) return;
   }
 }

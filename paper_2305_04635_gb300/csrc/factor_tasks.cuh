@@ -180,8 +180,12 @@ __device__ bool task_trsm(const FactorArgs& a, int I, int s, Smem<B>& sm, int* s
 // updated tile stays in registers (an R x R block per thread, rows ty+16r and
 // columns tx+16c).  On a diagonal tile (the DSYRK case) the blocks that lie
 // wholly above the diagonal are skipped.
+// With lis_in_smem, L_Is is already in sm.t0 (the same CTA has just solved it
+// with task_trsm, which leaves its result there) and is neither waited for nor
+// read again.
 template <int B>
-__device__ bool task_upd(const FactorArgs& a, int I, int J, int s, Smem<B>& sm, int* s_flag) {
+__device__ bool task_upd(const FactorArgs& a, int I, int J, int s, Smem<B>& sm, int* s_flag,
+                         bool lis_in_smem = false) {
   constexpr int R = B / 16;
   const int tid = threadIdx.x;
   const int s0I = first_step(a, I);
@@ -189,7 +193,7 @@ __device__ bool task_upd(const FactorArgs& a, int I, int J, int s, Smem<B>& sm, 
   // last (for UPD(I, s+1, s) it is the diagonal chain's TRSM), so it is waited
   // for and loaded after the others are already in flight.
   if (tid == 0) {
-    bool ok = wait_tile(a, I, s, s - s0I + 1);
+    bool ok = lis_in_smem || wait_tile(a, I, s, s - s0I + 1);
     if (ok) ok = wait_tile(a, I, J, s - s0I);
     *s_flag = ok;
   }
@@ -201,8 +205,10 @@ __device__ bool task_upd(const FactorArgs& a, int I, int J, int s, Smem<B>& sm, 
   // that the loads of L_Is are still in flight while L_Js is waited for.
   constexpr int E = B * B / kThreads;
   double li[E], lj[E];
+  if (!lis_in_smem) {
 #pragma unroll
-  for (int e = 0; e < E; ++e) li[e] = tile_elem(a.ab, a.ldab, a.n, a.k, I, s, tid + e * kThreads, B);
+    for (int e = 0; e < E; ++e) li[e] = tile_elem(a.ab, a.ldab, a.n, a.k, I, s, tid + e * kThreads, B);
+  }
   const int ty = tid / 16, tx = tid % 16;
   const bool diag = (I == J);
   double acc[R][R];
@@ -225,7 +231,7 @@ __device__ bool task_upd(const FactorArgs& a, int I, int J, int s, Smem<B>& sm, 
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int idx = tid + e * kThreads;
-    sA[idx] = li[e];
+    if (!lis_in_smem) sA[idx] = li[e];
     if (J != I) sB[idx] = lj[e];
   }
   const double* sBr = (J != I) ? sB : sA;

@@ -193,8 +193,8 @@ __host__ __device__ inline void decode_cp_ticket(const Schedule& a, long long t,
 // Order with the diagonal chain and two helper CTAs (p >= 2).  The helpers run,
 // for t = 2, 3, ..., the three tasks at distance two from the diagonal that the
 // chain's next inputs hang on:
-//     helper 1:  TRSM(t, t-2), then UPD(t, t, t-2)     (L(t, t-2) and the last outside update of A(t, t))
-//     helper 2:  UPD(t, t-1, t-2)                      (the last outside update of A(t, t-1))
+//     helper 2:  TRSM(t, t-2), then UPD(t, t-1, t-2)   (L(t, t-2) and the last outside update of A(t, t-1))
+//     helper 1:  UPD(t, t, t-2)                        (the last outside update of A(t, t))
 // so they no longer queue behind other tickets.  The tickets are the chain
 // order's without them:
 //     panel''(s) TRSM(s+2+r, s),      r = 1..m_s-2

@@ -73,13 +73,13 @@ def _is_chain(task):
 
 def _helper(task):
     """Helper CTA (1 or 2) that runs a task when the band holds two or more tiles below the diagonal,
-    else 0: helper 1 runs TRSM(s+2, s) and UPD(s+2, s+2, s), helper 2 runs UPD(s+2, s+1, s)."""
+    else 0: helper 2 runs TRSM(s+2, s) and UPD(s+2, s+1, s), helper 1 runs UPD(s+2, s+2, s)."""
     typ, s, I, J = task
     if I != s + 2:
         return 0
-    if typ == 1 or (typ == 2 and J == I):
+    if typ == 2 and J == I:
         return 1
-    return 2 if typ == 2 and J == s + 1 else 0
+    return 2 if typ == 1 or (typ == 2 and J == s + 1) else 0
 
 
 @pytest.mark.parametrize("workers", [1, 2, 5])
