@@ -190,7 +190,8 @@ __host__ __device__ inline void decode_cp_ticket(const Schedule& a, long long t,
 }
 
 // ----------------------------------------------------------------------------
-// Order with the diagonal chain and two helper CTAs (p >= 2).  The helpers run,
+// Order with the diagonal chain and two helper CTAs (defined for p >= 2; the
+// launch uses it for 2 <= p <= 40, see make_factor_plan).  The helpers run,
 // for t = 2, 3, ..., the three tasks at distance two from the diagonal that the
 // chain's next inputs hang on:
 //     helper 2:  TRSM(t, t-2), then UPD(t, t-1, t-2)   (L(t, t-2) and the last outside update of A(t, t-1))
