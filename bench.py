@@ -236,8 +236,8 @@ def run_ours(args, rank: int, world: int, dev: int):
     walls = gather_max(world, [wall, wall_e2e])
     wall, wall_e2e = walls
     F = sum(flops_eq1(n, k) for k in ks)
-    value = world * F * args.steps / wall / 1e9
-    e2e_value = world * F * args.steps / wall_e2e / 1e9
+    value = job_rate(world, F, args.steps, wall)
+    e2e_value = job_rate(world, F, args.steps, wall_e2e)
 
     hbm, hbm_kind = measured_hbm_gbs()
     per_k = {}
@@ -506,11 +506,18 @@ def barrier(world: int):
 
 
 def gather_max(world: int, vals: list[float]) -> list[float]:
+    """Element-wise maximum of vals over the ranks (the slowest rank's wall times)."""
     if world == 1:
         return vals
-    t = torch.tensor(vals, dtype=torch.float64, device="cuda")
+    dev = "cuda" if torch.distributed.get_backend() == "nccl" else "cpu"
+    t = torch.tensor(vals, dtype=torch.float64, device=dev)
     torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
     return t.tolist()
+
+
+def job_rate(world: int, flops_per_rank: float, steps: int, wall: float) -> float:
+    """Whole-job GFLOP/s of `world` replicas: every rank's flops over the slowest rank's time."""
+    return world * flops_per_rank * steps / wall / 1e9
 
 
 def main():
