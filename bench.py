@@ -54,7 +54,7 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one factor launch at n = 20000 for each sweep k, from
 # an ncu capture of dram__bytes_read.sum + dram__bytes_write.sum of this kernel;
 # traffic is proportional to n at fixed k, so it is scaled by n / 20000.
-TRAFFIC_N20000 = {50: 8.5e6, 100: 16.8e6, 200: 35.4e6, 500: 105.3e6, 1000: 258.4e6, 2000: 566.2e6}
+TRAFFIC_N20000 = {50: 8.5e6, 100: 16.8e6, 200: 35.6e6, 500: 105.7e6, 1000: 258.1e6, 2000: 569.3e6}
 
 
 def measured_hbm_gbs() -> tuple[float, str]:
