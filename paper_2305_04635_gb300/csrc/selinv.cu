@@ -406,7 +406,7 @@ __device__ bool sel_diag(const SelArgs& a, int J, Smem<B>& sm, int* s_flag) {
         part = sL[j * B + lane] * v;   // L(i,j) Sigma(i,j)
       }
 #pragma unroll
-      for (int off = 16; off >= 1; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+      for (int off = B / 2; off >= 1; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);   // rows are lanes < B
       if (lane == 0) sS[j * B + j] = (rl - (sE[j * B + j] + part)) * rl;
       if (lane > j && lane < jmax) sS[lane * B + j] = sS[j * B + lane];   // symmetric copy (row j)
       __syncwarp();
