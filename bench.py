@@ -51,6 +51,7 @@ KS = [50, 100, 200, 500, 1000, 2000]
 FP64_PEAK_TFLOPS = 1.25
 HBM_FALLBACK_GBS = 6800.0
 L2_FLUSH_BYTES = 256 << 20
+PRECISIONS = {"fp64": 0, "split": 3}
 # DRAM bytes (read + write) of one factor launch at n = 20000 for each sweep k, from
 # an ncu capture of dram__bytes_read.sum + dram__bytes_write.sum of this kernel;
 # traffic is proportional to n at fixed k, so it is scaled by n / 20000.
@@ -137,7 +138,8 @@ def run_ours(args, rank: int, world: int, dev: int):
     n = args.n
     data = make_inputs(n, ks)
     stream = torch.cuda.current_stream()
-    h = bchol.Handle()
+    h = bchol.Handle(tile=args.tile)
+    h.set_precision(PRECISIONS[args.precision])
     bufs = {}
     for k in ks:
         A, B = data[k]
@@ -531,6 +533,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-next", action="store_true", help="skip the batched, mixed and adjoint legs")
+    ap.add_argument("--tile", type=int, default=0, help="tile size (0: automatic)")
+    ap.add_argument("--precision", default="fp64", choices=sorted(PRECISIONS),
+                    help="trailing-update arithmetic: FP64 FMA, or FP64-accurate split products on the tensor cores")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -53,6 +53,27 @@ typedef enum {
   BCHOL_ERR_UNSUPPORTED = 5
 } bchol_status_t;
 
+/* Arithmetic of the factorization's trailing SYRK/GEMM updates (the O(n k^2)
+ * part of Algorithm 1, Sec. 3.2 and Eq. (1)), set per handle with
+ * bchol_set_precision.  POTRF and TRSM of the tiles are FP64 in every mode.
+ *   BCHOL_FP64         FP64 fused multiply-adds (the default; the paper's arithmetic).
+ *   BCHOL_FP32_UPDATE  updates accumulated in FP32 from FP32-rounded tiles (and
+ *                      FP32 panel TRSMs), and FP64 iterative refinement in the
+ *                      solve: bchol_factor then leaves ab holding A and keeps the
+ *                      mixed factor in the handle, and bchol_solve refines
+ *                      against that A (see bchol_set_precision).
+ *   BCHOL_TF32_UPDATE  not built; bchol_set_precision returns BCHOL_ERR_UNSUPPORTED.
+ *   BCHOL_FP64_SPLIT   FP64-accurate updates from exact bf16 digit products on the
+ *                      tensor cores (bchol_check_split_product), with tiles of 16
+ *                      and 32; with tiles of 64 the updates are FP64 FMA.  L
+ *                      agrees with the FP64 mode to rounding. */
+typedef enum {
+  BCHOL_FP64 = 0,
+  BCHOL_FP32_UPDATE = 1,
+  BCHOL_TF32_UPDATE = 2,
+  BCHOL_FP64_SPLIT = 3
+} bchol_precision_t;
+
 /* Create a handle bound to `stream` (a cudaStream_t; NULL = the legacy default
  * stream) on the current device.  No device memory is allocated here. */
 bchol_status_t bchol_create(bchol_handle_t* handle, void* stream);
@@ -83,7 +104,7 @@ size_t bchol_workspace_size(bchol_handle_t handle, int n, int k);
  *             pbtrf convention).  When j > 0 the contents of ab are unspecified.
  * The whole factorization is one persistent kernel launch (plus one memset
  * of the ready flags).  Tiles are b x b with b chosen from k (16 up to
- * k = 256, else 32) unless bchol_set_tile fixes it.
+ * k = 640, else 32) unless bchol_set_tile fixes it.
  */
 bchol_status_t bchol_factor(bchol_handle_t handle, int n, int k, double* ab, int ldab, int* info_dev);
 
@@ -97,15 +118,19 @@ bchol_status_t bchol_factor(bchol_handle_t handle, int n, int k, double* ab, int
  * ready flags) lives in one fixed 1 MiB array in the library's device memory,
  * which every GPU that loads the library holds until the process exits.
  *   stream      cudaStream_t to launch on (NULL = legacy default stream)
- *   n, k, ab, ldab, info_dev   as for bchol_factor (same kernel, same results)
+ *   n, k, ab, ldab, info_dev   as for bchol_factor; the kernel, and so the
+ *               result, is that of bchol_factor with the default settings
+ *               (automatic tile, FP64 precision mode)
  *   status_dev  device int owned by the caller: set to 0, then to
  *               BCHOL_ERR_TIMEOUT (2) if a bounded in-kernel wait ran out
  * Returns BCHOL_ERR_UNSUPPORTED, with nothing launched, when the problem needs
- * more scratch than the array holds (about 262000 tile ready flags: n = 1e5
- * with k up to a few thousand fits).  All calls on a device share the array,
- * so calls that overlap on the GPU race; order them.  The first call on each
- * device looks up the array's device address; make it before any stream
- * capture.
+ * more scratch than the array holds: 256 bytes plus 4 bytes per tile ready
+ * flag, ceil(n/b) * (ceil(k/b) + 1) flags with b = 16 for k <= 640, else 32.
+ * At n = 1e5 every k up to 2624 fits (k = 2625 does not); at n = 1e6, k up to
+ * 48.  All calls on a device share the array, so calls that overlap on the
+ * GPU race; order them.  The first call in each CUDA context looks up the
+ * array's device address: make it before any stream capture, and again after
+ * a cudaDeviceReset (which starts a new context).
  */
 bchol_status_t bchol_factor_noalloc(void* stream, int n, int k, double* ab, int ldab, int* info_dev,
                                     int* status_dev);
@@ -220,6 +245,35 @@ bchol_status_t bchol_get_info(bchol_handle_t handle, const int* info_dev, int co
  * budget of one in-kernel wait (default 2000 ms).  ctas_per_sm: persistent
  * CTAs per SM for the factor kernel (0 = automatic). */
 bchol_status_t bchol_set_tile(bchol_handle_t handle, int tile);
+
+/* Precision mode of the handle's factorizations (bchol_precision_t above).
+ * max_refine (>= 0) and tol (>= 0) bound the iterative refinement of
+ * BCHOL_FP32_UPDATE solves: corrections stop when the relative residual
+ * max_c ||b_c - A x_c|| / ||b_c|| is <= tol, stops shrinking, or after
+ * max_refine corrections; the other modes ignore them.  Returns BCHOL_ERR_ARG
+ * for an unknown mode or bad bounds, BCHOL_ERR_UNSUPPORTED for
+ * BCHOL_TF32_UPDATE (the mode is then unchanged).
+ * In the BCHOL_FP32_UPDATE mode (the steps of bchol_solve_mixed, split in two):
+ *   bchol_factor  equilibrates a copy of A in the handle's workspace,
+ *                 S A S with S = diag(A)^{-1/2}, and factors the copy with
+ *                 FP32-accumulated updates; ab is read, not overwritten, and
+ *                 info_dev is that factorization's info;
+ *   bchol_solve   must then be called with the same n, k, ab and ldab (ab
+ *                 still holding A) on the same handle, before any other
+ *                 factorization on it, else it returns BCHOL_ERR_ARG; it
+ *                 returns BCHOL_ERR_NOT_SPD if that factorization failed.  It
+ *                 overwrites B with X, refined in FP64 against A, 16 columns
+ *                 at a time, and synchronises the stream (the refinement
+ *                 reads residual norms on the host).
+ * The workspace of this mode holds the copy of the band besides the usual
+ * scratch (bchol_workspace_size accounts for it). */
+bchol_status_t bchol_set_precision(bchol_handle_t handle, bchol_precision_t precision, int max_refine, double tol);
+
+/* Refinement record of the last BCHOL_FP32_UPDATE bchol_solve on the handle:
+ * corrections made (the largest over its 16-column groups), final relative
+ * residual max_c ||b_c - A x_c|| / ||b_c|| and last relative correction
+ * max_c ||d_c|| / ||x_c||. */
+bchol_status_t bchol_last_refinement(bchol_handle_t handle, int* iters, double* resid, double* corr);
 bchol_status_t bchol_set_wait_limit_ms(bchol_handle_t handle, int wait_limit_ms);
 bchol_status_t bchol_set_ctas_per_sm(bchol_handle_t handle, int ctas_per_sm);
 
@@ -243,6 +297,12 @@ bchol_status_t bchol_set_stall_tile(bchol_handle_t handle, int I, int J);
  * ticket into (type, s, I, J) in tile units.  tile is 16, 32 or 64. */
 long long bchol_plan_task_count(int n, int k, int tile);
 bchol_status_t bchol_plan_task(int n, int k, int tile, long long ticket, int* type, int* s, int* I, int* J);
+/* The same for a precision mode: with BCHOL_FP64_SPLIT and tile 16 or 32 the
+ * updates of each block column run as strips, type 3 = STRIP(I, J, s): the
+ * updates UPD(I', J, s) of the tiles I' = I .. min(I+H-1, s+m), H = 128/tile. */
+long long bchol_plan_task_count_ex(int n, int k, int tile, int precision);
+bchol_status_t bchol_plan_task_ex(int n, int k, int tile, int precision, long long ticket, int* type, int* s, int* I,
+                                  int* J);
 
 /* The task order of the adjoint's selected inversion (bchol_backward), for
  * tests: the number of tasks for (n, k, tile) (or -1 on bad arguments), and
@@ -262,6 +322,25 @@ bchol_status_t bchol_adjoint_plan_task(int n, int k, int tile, long long ticket,
  * units in the last place; tests compare it with IEEE division.  Returns
  * BCHOL_ERR_ARG on a null handle or pointer with n > 0. */
 bchol_status_t bchol_check_pivot_rcp(bchol_handle_t handle, const double* x, double* y, int n);
+
+/* Self-check of the tensor-core split product that the BCHOL_FP64_SPLIT
+ * precision mode uses for the trailing updates A_IJ -= L_Is L_Js^T of
+ * Algorithm 1 (Sec. 3; the O(n k^2) part of Eq. (1)):
+ *     C := C - A B^T,  A m x 32, B n x 32, C m x n,
+ * all column-major device doubles owned by the caller (lda >= max(1,m),
+ * ldb >= max(1,n), ldc >= max(1,m); C may not overlap A or B).  Each FP64
+ * entry is cut into seven balanced 8-bit digits under a per-row power-of-two
+ * scale (Ozaki-style error-free splitting); the 28 digit products that carry
+ * FP64 precision run as exact bf16 MMAs with FP32 accumulation in tensor
+ * memory, and their sum is formed in 64-bit fixed point.  Each result is
+ * accurate to about 32 * 2^-54 * max_k |A(i,k)| * max_k |B(j,k)| plus the
+ * rounding of the FP64 update; integer-valued inputs whose products and sums
+ * fit in 53 bits give exact results.  A non-finite entry in row i of A or row j
+ * of B makes C(i,j) NaN.  Asynchronous on the handle's stream; a bounded
+ * in-kernel wait that runs out is reported by bchol_get_info as
+ * BCHOL_ERR_TIMEOUT.  Returns BCHOL_ERR_ARG on bad sizes or null pointers. */
+bchol_status_t bchol_check_split_product(bchol_handle_t handle, int m, int n, const double* A, int lda,
+                                         const double* B, int ldb, double* C, int ldc);
 
 /* Number of factor-kernel and solve-kernel launches made by the last call on
  * this handle (for launch accounting). */

@@ -29,6 +29,9 @@ _LIB_PATH = os.path.join(_HERE, "libbchol.so")
 _HEADER = os.path.join(os.path.dirname(_HERE), "include", "bchol.h")
 _lib = None
 
+# Precision modes (bchol_precision_t)
+FP64, FP32_UPDATE, TF32_UPDATE, FP64_SPLIT = 0, 1, 2, 3
+
 STATUS = {0: "BCHOL_OK", -1: "BCHOL_ERR_ARG", 1: "BCHOL_ERR_NOT_SPD", 2: "BCHOL_ERR_TIMEOUT",
           3: "BCHOL_ERR_CUDA", 4: "BCHOL_ERR_ALLOC", 5: "BCHOL_ERR_UNSUPPORTED"}
 
@@ -84,7 +87,12 @@ def load_library():
         "bchol_factor_batched": ([P, I, P, P, P, P, P, P, P, P], I),
         "bchol_plan_task_count": ([I, I, I], ctypes.c_longlong),
         "bchol_plan_task": ([I, I, I, ctypes.c_longlong, P, P, P, P], I),
+        "bchol_plan_task_count_ex": ([I, I, I, I], ctypes.c_longlong),
+        "bchol_plan_task_ex": ([I, I, I, I, ctypes.c_longlong, P, P, P, P], I),
+        "bchol_set_precision": ([P, I, I, ctypes.c_double], I),
+        "bchol_last_refinement": ([P, P, P, P], I),
         "bchol_check_pivot_rcp": ([P, P, P, I], I),
+        "bchol_check_split_product": ([P, I, I, P, I, P, I, P, I], I),
         "bchol_adjoint_plan_task_count": ([I, I, I], ctypes.c_longlong),
         "bchol_adjoint_plan_task": ([I, I, I, ctypes.c_longlong, P, P, P, P], I),
         "bchol_version": ([], ctypes.c_char_p),
@@ -128,6 +136,18 @@ class Handle:
 
     def set_tile(self, tile: int) -> None:
         _check("bchol_set_tile", self._lib.bchol_set_tile(self._h, tile))
+
+    def set_precision(self, precision: int, max_refine: int = 10, tol: float = 1e-10) -> None:
+        """Precision mode of the trailing updates (FP64, FP32_UPDATE, TF32_UPDATE, FP64_SPLIT)."""
+        _check("bchol_set_precision", self._lib.bchol_set_precision(self._h, precision, max_refine, tol))
+
+    def last_refinement(self) -> tuple[int, float, float]:
+        """(corrections, final relative residual, last relative correction) of the last
+        FP32_UPDATE solve on this handle."""
+        it, res, corr = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+        _check("bchol_last_refinement", self._lib.bchol_last_refinement(self._h, ctypes.byref(it), ctypes.byref(res),
+                                                                        ctypes.byref(corr)))
+        return it.value, res.value, corr.value
 
     def set_wait_limit_ms(self, ms: int) -> None:
         _check("bchol_set_wait_limit_ms", self._lib.bchol_set_wait_limit_ms(self._h, ms))
@@ -258,18 +278,19 @@ def get_info(info: torch.Tensor, handle: Handle | None = None) -> tuple[int, lis
     return int(rc), [int(host[i]) for i in range(count)]
 
 
-def plan_tasks(n: int, k: int, tile: int) -> list[tuple[int, int, int, int]]:
+def plan_tasks(n: int, k: int, tile: int, precision: int = FP64) -> list[tuple[int, int, int, int]]:
     """The factor kernel's task list in ticket order: (type, s, I, J) in tile units
-    (type 0 = POTRF, 1 = TRSM, 2 = UPD).  Host-side query; no GPU needed."""
+    (type 0 = POTRF, 1 = TRSM, 2 = UPD, 3 = STRIP of the updates of tiles I..I+3 in
+    column J).  Host-side query; no GPU needed."""
     lib = load_library()
-    total = lib.bchol_plan_task_count(n, k, tile)
+    total = lib.bchol_plan_task_count_ex(n, k, tile, precision)
     if total < 0:
         raise ValueError("bad arguments")
     out = []
     t, s, I, J = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     for ticket in range(total):
-        _check("bchol_plan_task", lib.bchol_plan_task(n, k, tile, ticket, ctypes.byref(t), ctypes.byref(s),
-                                                      ctypes.byref(I), ctypes.byref(J)))
+        _check("bchol_plan_task_ex", lib.bchol_plan_task_ex(n, k, tile, precision, ticket, ctypes.byref(t),
+                                                            ctypes.byref(s), ctypes.byref(I), ctypes.byref(J)))
         out.append((t.value, s.value, I.value, J.value))
     return out
 

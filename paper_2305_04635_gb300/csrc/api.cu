@@ -36,22 +36,32 @@ struct bchol_handle_s {
   int stall_I = -1, stall_J = -1;
   int* last_status = nullptr;  // status word of the workspace used last
   bchol_batch_t batch = nullptr;  // bchol_factor_batched's own plan
+  int precision = BCHOL_FP64;
+  int max_refine = 10;
+  double tol = 1e-10;
+  // BCHOL_FP32_UPDATE: the factorization that the next bchol_solve refines against
+  bool mixed_ready = false;
+  int mixed_n = 0, mixed_k = 0, mixed_ldab = 0;
+  const double* mixed_ab = nullptr;
+  const char* mixed_ws = nullptr;
+  const int* mixed_info = nullptr;
+  int last_iters = 0;
+  double last_resid = 0.0, last_corr = 0.0;
 };
 
 using namespace bchol;
 
-// Automatic tile size and CTAs per SM, from the n = 1e5 sweep on GB300:
-// b = 16 wins while the factorization is bound by its diagonal chain (whose
-// step time grows with b^3 on one SM) up to k of about 640; b = 32 wins above,
-// where the trailing updates dominate.  One CTA per SM while the ticket work
-// is small (k <= 256); two per SM above, to overlap the tasks' load and flag
-// latencies.
-static int auto_tile(int k) { return k <= 640 ? 16 : 32; }
-static int auto_ctas_per_sm(int k) { return k <= 256 ? 1 : 2; }
+// Does a precision mode run the split updates on the tensor cores?
+static bool split_mode(int precision) { return precision == BCHOL_FP64_SPLIT; }
+
+// Right-hand sides refined together by a BCHOL_FP32_UPDATE solve (its
+// workspace holds a copy of that many columns and their residuals).
+constexpr int kMixedChunk = 16;
 
 static size_t call_bytes(bchol_handle_t h, int n, int k) {
   const int kk = (n > 0 && k > n - 1) ? n - 1 : k;
   const int b = h->tile ? h->tile : auto_tile(kk);
+  if (h->precision == BCHOL_FP32_UPDATE && n > 0) return kStatusBytes + mixed_workspace_bytes(n, kk, kMixedChunk, b);
   const FactorPlan P = make_factor_plan(n, kk, b);
   size_t f = factor_workspace_bytes(P), s = solve_workspace_bytes(n, kk);
   return kStatusBytes + (f > s ? f : s);
@@ -72,6 +82,7 @@ static bchol_status_t get_workspace(bchol_handle_t h, size_t bytes, char** ws) {
       h->ws_own = nullptr;
       h->ws_own_bytes = 0;
       h->last_status = nullptr;
+      h->mixed_ready = false;
     }
     void* p = nullptr;
     if (cudaMalloc(&p, bytes) != cudaSuccess) {
@@ -89,7 +100,61 @@ static bchol_status_t get_workspace(bchol_handle_t h, size_t bytes, char** ws) {
   return BCHOL_OK;
 }
 
+// bchol_solve in the BCHOL_FP32_UPDATE mode: the factor of S A S that the last
+// bchol_factor left in the workspace, and refinement against A (ab still holds
+// A in this mode), kMixedChunk right-hand sides at a time; B is overwritten by X.
+static bchol_status_t solve_fp32_update(bchol_handle_t h, int n, int k, int nrhs, const double* ab, int ldab,
+                                        double* b, int ldb) {
+  const int kk = (n > 0 && k > n - 1) ? n - 1 : k;
+  const char* cur = h->ws_lent ? static_cast<const char*>(h->ws_lent) : static_cast<const char*>(h->ws_own);
+  if (!h->mixed_ready || h->mixed_n != n || h->mixed_k != kk || h->mixed_ab != ab || h->mixed_ldab != ldab ||
+      h->mixed_ws != cur)
+    return BCHOL_ERR_ARG;  // no matching bchol_factor on this handle
+  int info = 0;
+  if (cudaMemcpyAsync(&info, h->mixed_info, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return BCHOL_ERR_CUDA;
+  if (info != 0) return BCHOL_ERR_NOT_SPD;
+  char* ws = const_cast<char*>(cur) + kStatusBytes;
+  const int tile = h->tile ? h->tile : auto_tile(kk);
+  double* b0 = mixed_rhs_copy(ws, n, kk, kMixedChunk, tile);
+  int launches = 0, iters = 0;
+  double resid = 0.0, corr = 0.0;
+  for (int c0 = 0; c0 < nrhs; c0 += kMixedChunk) {
+    const int nc = nrhs - c0 < kMixedChunk ? nrhs - c0 : kMixedChunk;
+    double* bc = b + (long long)c0 * ldb;
+    if (cudaMemcpy2DAsync(b0, sizeof(double) * n, bc, sizeof(double) * ldb, sizeof(double) * n, nc,
+                          cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+      return BCHOL_ERR_CUDA;
+    int it = 0, l = 0;
+    double rs = 0.0, cr = 0.0;
+    const int r = mixed_refine(n, kk, nc, ab, ldab, b0, n, bc, ldb, h->max_refine, h->tol, tile, ws, kMixedChunk,
+                               h->stream, &it, &rs, &cr, &l, nullptr);
+    if (r != BCHOL_OK) {
+      cudaGetLastError();
+      return static_cast<bchol_status_t>(r);
+    }
+    launches += l + 1;
+    iters = iters > it ? iters : it;
+    resid = resid > rs ? resid : rs;
+    corr = corr > cr ? corr : cr;
+  }
+  h->last_iters = iters;
+  h->last_resid = resid;
+  h->last_corr = corr;
+  h->last_launches = launches;
+  return BCHOL_OK;
+}
+
 extern "C" {
+
+bchol_status_t bchol_last_refinement(bchol_handle_t h, int* iters, double* resid, double* corr) {
+  if (!h || !iters || !resid || !corr) return BCHOL_ERR_ARG;
+  *iters = h->last_iters;
+  *resid = h->last_resid;
+  *corr = h->last_corr;
+  return BCHOL_OK;
+}
 
 bchol_status_t bchol_create(bchol_handle_t* handle, void* stream) {
   if (!handle) return BCHOL_ERR_ARG;
@@ -120,6 +185,7 @@ bchol_status_t bchol_set_stream(bchol_handle_t h, void* stream) {
 
 bchol_status_t bchol_set_workspace(bchol_handle_t h, void* ptr, size_t bytes) {
   if (!h) return BCHOL_ERR_ARG;
+  h->mixed_ready = false;
   if (ptr == nullptr || bytes == 0) {
     h->ws_lent = nullptr;
     h->ws_lent_bytes = 0;
@@ -145,6 +211,25 @@ bchol_status_t bchol_set_tile(bchol_handle_t h, int tile) {
   return BCHOL_OK;
 }
 
+bchol_status_t bchol_set_precision(bchol_handle_t h, bchol_precision_t precision, int max_refine, double tol) {
+  if (!h || max_refine < 0 || !(tol >= 0.0)) return BCHOL_ERR_ARG;
+  switch (precision) {
+    case BCHOL_FP64:
+    case BCHOL_FP64_SPLIT:
+    case BCHOL_FP32_UPDATE:
+      break;
+    case BCHOL_TF32_UPDATE:
+      return BCHOL_ERR_UNSUPPORTED;
+    default:
+      return BCHOL_ERR_ARG;
+  }
+  if (precision != h->precision) h->mixed_ready = false;
+  h->precision = precision;
+  h->max_refine = max_refine;
+  h->tol = tol;
+  return BCHOL_OK;
+}
+
 bchol_status_t bchol_set_wait_limit_ms(bchol_handle_t h, int ms) {
   if (!h || ms < 1) return BCHOL_ERR_ARG;
   h->wait_ms = ms;
@@ -165,14 +250,25 @@ bchol_status_t bchol_set_stall_tile(bchol_handle_t h, int I, int J) {
 }
 
 long long bchol_plan_task_count(int n, int k, int tile) {
-  if (n < 0 || k < 0 || !(tile == 16 || tile == 32 || tile == 64)) return -1;
-  return (long long)make_factor_plan(n, k, tile).total;
+  return bchol_plan_task_count_ex(n, k, tile, BCHOL_FP64);
 }
 
 bchol_status_t bchol_plan_task(int n, int k, int tile, long long ticket, int* type, int* s, int* I, int* J) {
-  if (n < 0 || k < 0 || !(tile == 16 || tile == 32 || tile == 64) || !type || !s || !I || !J) return BCHOL_ERR_ARG;
-  const FactorPlan P = make_factor_plan(n, k, tile);
-  if (ticket < 0 || (unsigned long long)ticket >= P.total) return BCHOL_ERR_ARG;
+  return bchol_plan_task_ex(n, k, tile, BCHOL_FP64, ticket, type, s, I, J);
+}
+
+long long bchol_plan_task_count_ex(int n, int k, int tile, int precision) {
+  if (n < 0 || k < 0 || !(tile == 16 || tile == 32 || tile == 64) || precision < 0 || precision > 3) return -1;
+  return plan_task_count(make_factor_plan(n, k, tile, split_mode(precision)));
+}
+
+bchol_status_t bchol_plan_task_ex(int n, int k, int tile, int precision, long long ticket, int* type, int* s, int* I,
+                                  int* J) {
+  if (n < 0 || k < 0 || !(tile == 16 || tile == 32 || tile == 64) || precision < 0 || precision > 3 || !type || !s ||
+      !I || !J)
+    return BCHOL_ERR_ARG;
+  const FactorPlan P = make_factor_plan(n, k, tile, split_mode(precision));
+  if (ticket < 0 || ticket >= plan_task_count(P)) return BCHOL_ERR_ARG;
   plan_task(P, ticket, *type, *s, *I, *J);
   return BCHOL_OK;
 }
@@ -200,6 +296,28 @@ bchol_status_t bchol_check_pivot_rcp(bchol_handle_t h, const double* x, double* 
   return BCHOL_OK;
 }
 
+bchol_status_t bchol_check_split_product(bchol_handle_t h, int m, int n, const double* A, int lda, const double* B,
+                                         int ldb, double* C, int ldc) {
+  if (!h || m < 0 || n < 0 || lda < (m > 1 ? m : 1) || ldb < (n > 1 ? n : 1) || ldc < (m > 1 ? m : 1))
+    return BCHOL_ERR_ARG;
+  if (m > 0 && n > 0 && (!A || !B || !C)) return BCHOL_ERR_ARG;
+  h->last_launches = 0;
+  if (m == 0 || n == 0) return BCHOL_OK;
+  char* ws = nullptr;
+  bchol_status_t rc = get_workspace(h, kStatusBytes, &ws);
+  if (rc != BCHOL_OK) return rc;
+  int* status = reinterpret_cast<int*>(ws);
+  h->last_status = status;
+  if (cudaMemsetAsync(status + 1, 0, sizeof(int), h->stream) != cudaSuccess) return BCHOL_ERR_CUDA;
+  if (launch_split_check(m, n, A, lda, B, ldb, C, ldc, status, status + 1, (uint64_t)h->wait_ms * 1000000ull,
+                         h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return BCHOL_ERR_CUDA;
+  }
+  h->last_launches = 1;
+  return BCHOL_OK;
+}
+
 int bchol_last_launch_count(bchol_handle_t h) { return h ? h->last_launches : 0; }
 
 const char* bchol_version(void) { return "bchol 0.1.0 (sm_103a)"; }
@@ -213,9 +331,29 @@ bchol_status_t bchol_factor(bchol_handle_t h, int n, int k, double* ab, int ldab
   bchol_status_t rc = get_workspace(h, call_bytes(h, n, k), &ws);
   if (rc != BCHOL_OK) return rc;
   const int b = h->tile ? h->tile : auto_tile(kk);
-  const FactorPlan P = make_factor_plan(n, kk, b);
   int* status = reinterpret_cast<int*>(ws);
   h->last_status = status;
+  if (h->precision == BCHOL_FP32_UPDATE) {
+    h->mixed_ready = false;
+    int launches = 0;
+    const int r = mixed_factor(n, kk, ab, ldab, info_dev, b, h->ctas_per_sm ? h->ctas_per_sm : auto_ctas_per_sm(kk),
+                               ws + kStatusBytes, kMixedChunk, status, (uint64_t)h->wait_ms * 1000000ull, h->stream,
+                               &launches);
+    if (r != BCHOL_OK) {
+      cudaGetLastError();
+      return static_cast<bchol_status_t>(r);
+    }
+    h->mixed_ready = true;
+    h->mixed_n = n;
+    h->mixed_k = kk;
+    h->mixed_ab = ab;
+    h->mixed_ldab = ldab;
+    h->mixed_ws = ws;
+    h->mixed_info = info_dev;
+    h->last_launches = launches;
+    return BCHOL_OK;
+  }
+  const FactorPlan P = make_factor_plan(n, kk, b, split_mode(h->precision));
   cudaError_t e = launch_factor(P, ab, ldab, info_dev, ws + kStatusBytes, status,
                                 (uint64_t)h->wait_ms * 1000000ull, h->ctas_per_sm ? h->ctas_per_sm : auto_ctas_per_sm(kk),
                                 h->stall_I, h->stall_J, h->stream);
@@ -233,6 +371,7 @@ bchol_status_t bchol_solve(bchol_handle_t h, int n, int k, int nrhs, const doubl
   if (n > 0 && nrhs > 0 && (!ab || !b)) return BCHOL_ERR_ARG;
   h->last_launches = 0;
   if (n == 0 || nrhs == 0) return BCHOL_OK;
+  if (h->precision == BCHOL_FP32_UPDATE) return solve_fp32_update(h, n, k, nrhs, ab, ldab, b, ldb);
   char* ws = nullptr;
   bchol_status_t rc = get_workspace(h, call_bytes(h, n, k), &ws);
   if (rc != BCHOL_OK) return rc;

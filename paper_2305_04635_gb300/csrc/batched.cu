@@ -73,6 +73,7 @@ __device__ __forceinline__ FactorArgs matrix_args(const BatchArgs& g, int m) {
   a.info = M.info;
   a.wait_ns = g.wait_ns;
   a.stall = -1;
+  a.H = 1;
   return a;
 }
 

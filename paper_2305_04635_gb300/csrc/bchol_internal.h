@@ -10,6 +10,15 @@ namespace bchol {
 constexpr int kStatusOk = 0;
 constexpr int kStatusTimeout = 2;
 
+// Automatic tile size and CTAs per SM, from the n = 1e5 sweep on GB300:
+// b = 16 wins while the factorization is bound by its diagonal chain (whose
+// step time grows with b^3 on one SM) up to k of about 640; b = 32 wins above,
+// where the trailing updates dominate.  One CTA per SM while the ticket work
+// is small (k <= 256); two per SM above, to overlap the tasks' load and flag
+// latencies.  bchol_factor and bchol_factor_noalloc both use this rule.
+inline int auto_tile(int k) { return k <= 640 ? 16 : 32; }
+inline int auto_ctas_per_sm(int k) { return k <= 256 ? 1 : 2; }
+
 // Tile geometry of one factorization: S = ceil(n/b) tile rows, p = ceil(k/b)
 // sub-diagonal tiles per panel (clamped to S-1).
 struct FactorPlan {
@@ -24,11 +33,16 @@ struct FactorPlan {
   unsigned long long total = 0;  // tasks of the whole factorization
   size_t flag_count = 0;       // ints of ready flags: S*(p+1)
   bool f32_update = false;     // mixed precision: trailing updates accumulated in FP32
+  int H = 1;                   // > 1: the updates run as strips of H = 128 / b tiles, split products on the tensor cores
 };
 
-FactorPlan make_factor_plan(int n, int k, int b);
-// Task t (0-based) of the combined order that one factorization runs.
+// Plan of one factorization with tiles of b; `split` selects the tensor-core
+// split updates (tiles of 16 and 32; tiles of 64 ignore it).
+FactorPlan make_factor_plan(int n, int k, int b, bool split = false);
+// Task t (0-based) of the combined order that one factorization runs, and the
+// number of tasks in that order.
 void plan_task(const FactorPlan& P, long long t, int& type, int& s, int& I, int& J);
+long long plan_task_count(const FactorPlan& P);
 
 // Device workspace needed by one factorization (control block + flags).
 size_t factor_workspace_bytes(const FactorPlan& plan);
@@ -50,6 +64,11 @@ cudaError_t launch_solve_f32(int n, int k, int nrhs, const double* ab, long long
 
 int num_sms();
 
+// The tensor-core split product alone (split.cu): C := C - A B^T, inner dimension 32.
+cudaError_t launch_split_check(int m, int n, const double* A, long long lda, const double* B, long long ldb,
+                               double* C, long long ldc, int* status, int* abort_word, uint64_t wait_ns,
+                               cudaStream_t stream);
+
 // Adjoint (selinv.cu): band of A^{-1} by selected inversion and the band gradient.
 size_t selinv_workspace_bytes(int n, int k, int b);
 long long adjoint_plan_count(int n, int k, int b);
@@ -61,6 +80,13 @@ cudaError_t launch_logdet(const double* ab, long long ldab, int n, double* out, 
 
 // Mixed-precision factor + FP64 iterative refinement (mixed.cu).
 size_t mixed_workspace_bytes(int n, int k, int nrhs, int tile);
+// The workspace's copy of up to nrhs_max right-hand sides (mixed_layout's B0).
+double* mixed_rhs_copy(void* ws, int n, int k, int nrhs_max, int tile);
+int mixed_factor(int n, int k, const double* ab, long long ldab, int* info_dev, int tile, int ctas_per_sm, void* ws,
+                 int nrhs_max, int* status, uint64_t wait_ns, cudaStream_t stream, int* launches_out);
+int mixed_refine(int n, int k, int nrhs, const double* ab, long long ldab, const double* b, long long ldb, double* x,
+                 long long ldx, int max_iter, double tol, int tile, void* ws, int nrhs_max, cudaStream_t stream,
+                 int* iters_out, double* resid_out, double* corr_out, int* launches_out, double* phase_ms);
 int mixed_solve(int n, int k, int nrhs, const double* ab, long long ldab, const double* b, long long ldb, double* x,
                 long long ldx, int max_iter, double tol, int* info_dev, int tile, int ctas_per_sm, void* ws,
                 int* status, uint64_t wait_ns, cudaStream_t stream, int* iters_out, double* resid_out,

@@ -39,6 +39,7 @@
 #include <cstdio>
 
 #include "diag_chain.cuh"
+#include "strip_task.cuh"
 
 namespace bchol {
 
@@ -73,12 +74,17 @@ __device__ void factor_helper(const FactorArgs& a, Smem<B>& sm, int* s_flag, int
 }
 
 // MODE 0: tickets only; 1: the diagonal chain (CTA 0) and tickets; 2: the chain,
-// two helpers (CTAs 1 and 2) and tickets.
-template <int B, bool F32, int MODE>
+// two helpers (CTAs 1 and 2) and tickets.  TC: the update tickets are strips,
+// split products on the tensor cores (strip_task.cuh); each ticket CTA holds
+// 256 (tiles of 32) or 128 (tiles of 16) columns of tensor memory for its
+// lifetime.
+template <int B, bool F32, int MODE, bool TC>
 __global__ void __launch_bounds__(kThreads, 2) factor_kernel(FactorArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ long long s_task;
   __shared__ int s_flag;
+  __shared__ unsigned long long s_mbar;
+  __shared__ uint32_t s_tmem;
   if constexpr (MODE >= 1) {
     if (blockIdx.x == 0) {
       if (threadIdx.x == 0) st_release(&a.ctl->chain_sm, sm_id() + 1);
@@ -115,6 +121,8 @@ __global__ void __launch_bounds__(kThreads, 2) factor_kernel(FactorArgs a) {
     if (s_flag) return;
   }
   Smem<B>& sm = *reinterpret_cast<Smem<B>*>(smem_raw);
+  split::Ctx cx{};
+  if constexpr (TC) cx = split::ctx_begin<B>(&s_mbar, &s_tmem);
   unsigned long long next = 0;
   if (threadIdx.x == 0) next = atomicAdd(&a.ctl->ticket, 1ULL);
   while (true) {
@@ -125,13 +133,20 @@ __global__ void __launch_bounds__(kThreads, 2) factor_kernel(FactorArgs a) {
     if (threadIdx.x == 0) next = atomicAdd(&a.ctl->ticket, 1ULL);  // claim the next task early
     int type, s, I, J;
     if constexpr (MODE == 2)
-      decode_hp_ticket(Schedule{a.S, a.p, a.Sreg, a.Treg}, t, type, s, I, J);
+      decode_hp_ticket(Schedule{a.S, a.p, a.Sreg, a.Treg, a.H}, t, type, s, I, J);
     else if constexpr (MODE == 1)
-      decode_cp_ticket(Schedule{a.S, a.p, a.Sreg, a.Treg}, t, type, s, I, J);
+      decode_cp_ticket(Schedule{a.S, a.p, a.Sreg, a.Treg, a.H}, t, type, s, I, J);
     else
       decode_task(Schedule{a.S, a.p, a.Sreg, a.Treg}, t, type, s, I, J);
+    if constexpr (TC) {
+      if (type == kStrip) {
+        if (!task_strip<B>(a, I, J, s, *reinterpret_cast<split::Smem<B>*>(smem_raw), cx, &s_flag)) break;
+        continue;
+      }
+    }
     if (!run_task<B, F32>(a, type, s, I, J, sm, &s_flag)) break;
   }
+  if constexpr (TC) split::ctx_end<B>(cx);
 }
 
 __global__ void pivot_rcp_kernel(const double* x, double* y, int n) {
@@ -145,8 +160,9 @@ cudaError_t launch_pivot_rcp(const double* x, double* y, int n, cudaStream_t str
   return cudaGetLastError();
 }
 
-FactorPlan make_factor_plan(int n, int k, int b) {
+FactorPlan make_factor_plan(int n, int k, int b, bool split) {
   FactorPlan P;
+  P.H = (split && (b == 16 || b == 32)) ? split::kRowsA / b : 1;
   P.n = n;
   P.k = (n > 0 && k > n - 1) ? n - 1 : k;
   P.b = b;
@@ -162,17 +178,20 @@ FactorPlan make_factor_plan(int n, int k, int b) {
   for (int s = (int)P.Sreg; s < P.S; ++s) total += (unsigned long long)sched_block_size(sc, s);
   P.total = total;
   P.flag_count = (size_t)P.S * (size_t)(P.p + 1);
-  P.Treg_cp = cp_treg(P.p);
-  const Schedule cs{P.S, P.p, P.Sreg, P.Treg_cp};
+  P.Treg_cp = cp_treg(P.p, P.H);
+  const Schedule cs{P.S, P.p, P.Sreg, P.Treg_cp, P.H};
   unsigned long long tickets = (unsigned long long)cp_panel0(cs);
   tickets += (unsigned long long)P.Sreg * (unsigned long long)P.Treg_cp;
   for (int s = (int)P.Sreg; s < P.S; ++s) tickets += (unsigned long long)cp_block_size(cs, s);
   P.total_cp = tickets;
   // Helpers pay off while the chain bounds the launch; with many tiles per
-  // panel (k = 2000 at b = 32) the two CTAs are worth more as ticket CTAs.
-  P.helper = (b <= 32 && P.p >= 2 && P.p <= 40);
-  P.Treg_hp = hp_treg(P.p);
-  const Schedule hs{P.S, P.p, P.Sreg, P.Treg_hp};
+  // panel (k = 2000 at b = 32) and FP64 updates the two CTAs are worth more
+  // as ticket CTAs.
+  // With the split updates the trailing update is cheap at every k, so the
+  // chain's inputs always get the helpers.
+  P.helper = (b <= 32 && P.p >= 2 && (P.p <= 40 || P.H > 1));
+  P.Treg_hp = hp_treg(P.p, P.H);
+  const Schedule hs{P.S, P.p, P.Sreg, P.Treg_hp, P.H};
   tickets = (unsigned long long)hp_panel0(hs);
   tickets += (unsigned long long)P.Sreg * (unsigned long long)P.Treg_hp;
   for (int s = (int)P.Sreg; s < P.S; ++s) tickets += (unsigned long long)hp_block_size(hs, s);
@@ -182,23 +201,52 @@ FactorPlan make_factor_plan(int n, int k, int b) {
 
 size_t factor_workspace_bytes(const FactorPlan& P) { return 256 + P.flag_count * sizeof(int); }
 
-template <int B, bool F32, int MODE>
+template <int B, bool F32, int MODE, bool TC = false>
 static cudaError_t launch_b(const FactorArgs& a, int ctas_per_sm, cudaStream_t stream) {
   size_t smem = sizeof(Smem<B>);
   if constexpr (MODE >= 1) smem = std::max(smem, sizeof(DiagSmem<B, F32>));
+  if constexpr (TC) smem = std::max(smem, sizeof(split::Smem<B>));
   cudaError_t e =
-      cudaFuncSetAttribute(factor_kernel<B, F32, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(factor_kernel<B, F32, MODE, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  // The split products' 72 KB per CTA fit two CTAs per SM only with the
+  // largest shared-memory carveout; ask for it, or the occupancy (and the
+  // grid) is computed for a smaller one.
+  if constexpr (TC) {
+    e = cudaFuncSetAttribute(factor_kernel<B, F32, MODE, TC>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+  }
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, factor_kernel<B, F32, MODE>, kThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, factor_kernel<B, F32, MODE, TC>, kThreads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+  // The occupancy query answers 1 for any kernel that allocates tensor memory,
+  // whatever it allocates; the SM runs as many CTAs as its registers, shared
+  // memory and threads allow, and tcgen05.alloc waits for columns.  So the
+  // split kernels size their grid from those resources and from the tensor
+  // memory: each ticket CTA holds 256 (tiles of 32) or 128 (tiles of 16) of the
+  // SM's 512 columns.
+  if constexpr (TC) {
+    cudaFuncAttributes fa;
+    int dev = 0, smem_sm = 0, regs_sm = 0, reserved = 0;
+    if (cudaFuncGetAttributes(&fa, factor_kernel<B, F32, MODE, TC>) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess)
+      return cudaErrorInvalidConfiguration;
+    const int regs_cta = (fa.numRegs + 7) / 8 * 8 * kThreads;
+    const int smem_cta = (int)(smem + fa.sharedSizeBytes) + reserved;
+    int fit = std::min(regs_sm / std::max(regs_cta, 1), smem_sm / std::max(smem_cta, 1));
+    fit = std::min({fit, 2048 / kThreads, (int)(512 / split::tmem_cols<B>())});
+    per_sm = std::max(1, ctas_per_sm > 0 ? std::min(fit, ctas_per_sm) : fit);
+  }
   long long grid = (long long)per_sm * num_sms();
   const unsigned long long need = a.total + (MODE == 2 ? 3 : MODE == 1 ? 1 : 0);  // tickets + chain (+ helpers)
   if ((unsigned long long)grid > need) grid = (long long)need;
   if (grid < 1) grid = 1;
-  factor_kernel<B, F32, MODE><<<(unsigned)grid, kThreads, smem, stream>>>(a);
+  factor_kernel<B, F32, MODE, TC><<<(unsigned)grid, kThreads, smem, stream>>>(a);
   return cudaGetLastError();
 }
 
@@ -224,6 +272,7 @@ cudaError_t launch_factor(const FactorPlan& P, double* ab, long long ldab, int* 
   a.info = info;
   a.wait_ns = wait_ns;
   a.stall = -1;
+  a.H = P.H;
   if (stall_I >= 0 && stall_J >= 0 && stall_I < P.S && stall_J <= stall_I && stall_I - stall_J <= P.p)
     a.stall = stall_J * (P.p + 1) + (stall_I - stall_J);
   if (P.b <= 32) {  // diagonal chain (+ helpers) + tickets
@@ -239,12 +288,26 @@ cudaError_t launch_factor(const FactorPlan& P, double* ab, long long ldab, int* 
       default: return cudaErrorInvalidValue;
     }
   }
+  if (P.b == 32 && P.H > 1)
+    return h ? launch_b<32, false, 2, true>(a, ctas_per_sm, stream) : launch_b<32, false, 1, true>(a, ctas_per_sm, stream);
+  if (P.b == 16 && P.H > 1)
+    return h ? launch_b<16, false, 2, true>(a, ctas_per_sm, stream) : launch_b<16, false, 1, true>(a, ctas_per_sm, stream);
   switch (P.b) {
     case 16: return h ? launch_b<16, false, 2>(a, ctas_per_sm, stream) : launch_b<16, false, 1>(a, ctas_per_sm, stream);
     case 32: return h ? launch_b<32, false, 2>(a, ctas_per_sm, stream) : launch_b<32, false, 1>(a, ctas_per_sm, stream);
     case 64: return launch_b<64, false, 0>(a, ctas_per_sm, stream);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// Tasks in the combined order: all tasks of the tiled factorization with one
+// update per tile, fewer when the updates run as strips.
+long long plan_task_count(const FactorPlan& P) {
+  if (P.b > 32 || P.H == 1 || P.n <= 0) return (long long)P.total;
+  const long long nd = P.p >= 1 ? 3 : 1;
+  long long c = 1 + (long long)(P.S - 1) * nd;
+  if (P.helper && P.S > 2) c += 3LL * (P.S - 2);
+  return c + (long long)(P.helper ? P.total_hp : P.total_cp);
 }
 
 // The combined task order of one factorization (host side): for tiles of 16
@@ -255,7 +318,7 @@ void plan_task(const FactorPlan& P, long long t, int& type, int& s, int& I, int&
     decode_task(Schedule{P.S, P.p, P.Sreg, P.Treg}, t, type, s, I, J);
     return;
   }
-  const Schedule cs{P.S, P.p, P.Sreg, P.helper ? P.Treg_hp : P.Treg_cp};
+  const Schedule cs{P.S, P.p, P.Sreg, P.helper ? P.Treg_hp : P.Treg_cp, P.H};
   auto ticket = [&](long long u) {
     if (P.helper)
       decode_hp_ticket(cs, u, type, s, I, J);

@@ -136,76 +136,125 @@ using namespace bchol;
 
 namespace bchol {
 
-// Mixed-precision solve; the workspace `ws` is laid out by mixed_workspace_bytes.
-size_t mixed_workspace_bytes(int n, int k, int nrhs, int tile) {
-  auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
-  const FactorPlan P = make_factor_plan(n, k, tile);
-  return up(sizeof(double) * (size_t)(k + 1) * n) + up(sizeof(double) * n) + up(sizeof(double) * (size_t)n * nrhs) +
-         up(sizeof(double) * 4 * (size_t)nrhs) + up(factor_workspace_bytes(P)) + up(solve_workspace_bytes(n, k));
+// Workspace of the mixed path, in this order: the equilibrated copy F of the
+// band, the scale vector s, a copy B0 of up to nrhs right-hand sides (used when
+// the solution overwrites them), the residual block R, the norms, and the
+// factor/solve scratch.  The factorization writes F and s only, so a later
+// solve with the same (n, k) finds them in place.
+struct MixedWs {
+  double* F;
+  double* s;
+  double* B0;
+  double* R;
+  double* nrm;
+  void* fws;
+  void* sws;
+};
+
+static size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
+
+static MixedWs mixed_layout(void* wsp, int n, int k, int nrhs, int tile) {
+  char* ws = static_cast<char*>(wsp);
+  MixedWs m;
+  m.F = reinterpret_cast<double*>(ws);
+  ws += up256(sizeof(double) * (size_t)(k + 1) * n);
+  m.s = reinterpret_cast<double*>(ws);
+  ws += up256(sizeof(double) * n);
+  m.B0 = reinterpret_cast<double*>(ws);
+  ws += up256(sizeof(double) * (size_t)n * nrhs);
+  m.R = reinterpret_cast<double*>(ws);
+  ws += up256(sizeof(double) * (size_t)n * nrhs);
+  m.nrm = reinterpret_cast<double*>(ws);  // [0,nrhs): ||b||^2, then ||r||^2, ||d||^2, ||x||^2
+  ws += up256(sizeof(double) * 4 * (size_t)nrhs);
+  m.fws = ws;
+  ws += up256(factor_workspace_bytes(make_factor_plan(n, k, tile)));
+  m.sws = ws;
+  return m;
 }
 
-int mixed_solve(int n, int k, int nrhs, const double* ab, long long ldab, const double* b, long long ldb, double* x,
-                long long ldx, int max_iter, double tol, int* info_dev, int tile, int ctas_per_sm, void* wsp,
-                int* status, uint64_t wait_ns, cudaStream_t st, int* iters_out, double* resid_out,
-                double* corr_out, int* launches_out) {
-  auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
-  char* ws = static_cast<char*>(wsp);
-  double* F = reinterpret_cast<double*>(ws);
-  ws += up(sizeof(double) * (size_t)(k + 1) * n);
-  double* s = reinterpret_cast<double*>(ws);
-  ws += up(sizeof(double) * n);
-  double* R = reinterpret_cast<double*>(ws);
-  ws += up(sizeof(double) * (size_t)n * nrhs);
-  double* nrm = reinterpret_cast<double*>(ws);   // [0,nrhs): ||b||^2, then ||r||^2, ||d||^2, ||x||^2
-  ws += up(sizeof(double) * 4 * (size_t)nrhs);
+double* mixed_rhs_copy(void* ws, int n, int k, int nrhs_max, int tile) {
+  return mixed_layout(ws, n, k, nrhs_max, tile).B0;
+}
+
+size_t mixed_workspace_bytes(int n, int k, int nrhs, int tile) {
+  const FactorPlan P = make_factor_plan(n, k, tile);
+  return up256(sizeof(double) * (size_t)(k + 1) * n) + up256(sizeof(double) * n) +
+         2 * up256(sizeof(double) * (size_t)n * nrhs) + up256(sizeof(double) * 4 * (size_t)nrhs) +
+         up256(factor_workspace_bytes(P)) + up256(solve_workspace_bytes(n, k));
+}
+
+// Equilibrate A into F and factor F with FP32-accumulated updates (asynchronous:
+// info_dev is written by the kernel).
+int mixed_factor(int n, int k, const double* ab, long long ldab, int* info_dev, int tile, int ctas_per_sm, void* wsp,
+                 int nrhs_max, int* status, uint64_t wait_ns, cudaStream_t st, int* launches_out) {
+  const MixedWs m = mixed_layout(wsp, n, k, nrhs_max, tile);
   FactorPlan P = make_factor_plan(n, k, tile);
   P.f32_update = true;
-  void* fws = ws;
-  ws += up(factor_workspace_bytes(P));
-  void* sws = ws;
+  const int T = 256;
+  const unsigned gn = (unsigned)((n + T - 1) / T);
+  equil_scale_kernel<<<gn, T, 0, st>>>(ab, ldab, n, m.s);
+  const long long nb = (long long)(k + 1) * n;
+  equil_copy_kernel<<<(unsigned)((nb + T - 1) / T), T, 0, st>>>(ab, ldab, n, k, m.s, m.F, k + 1);
+  if (cudaGetLastError() != cudaSuccess) return BCHOL_ERR_CUDA;
+  if (launch_factor(P, m.F, k + 1, info_dev, m.fws, status, wait_ns, ctas_per_sm, -1, -1, st) != cudaSuccess)
+    return BCHOL_ERR_CUDA;
+  *launches_out = 3;
+  return BCHOL_OK;
+}
+
+// x from b by the factor in the workspace and FP64 refinement against A.
+// nrhs <= the nrhs_max the workspace was laid out for.  Synchronises.
+int mixed_refine(int n, int k, int nrhs, const double* ab, long long ldab, const double* b, long long ldb, double* x,
+                 long long ldx, int max_iter, double tol, int tile, void* wsp, int nrhs_max, cudaStream_t st,
+                 int* iters_out, double* resid_out, double* corr_out, int* launches_out, double* phase_ms) {
+  const MixedWs m = mixed_layout(wsp, n, k, nrhs_max, tile);
+  double* R = m.R;
+  double* nrm = m.nrm;
   const long long ldf = k + 1;
   int launches = 0;
   const int T = 256;
   const unsigned gn = (unsigned)((n + T - 1) / T);
   std::vector<double> h(4 * (size_t)nrhs);
   cudaError_t e;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  if (phase_ms) {
+    for (auto& v : ev) cudaEventCreate(&v);
+    phase_ms[0] = phase_ms[1] = 0.0;
+  }
+  auto tic = [&]() { if (phase_ms) cudaEventRecord(ev[0], st); };
+  auto toc = [&](int which) {
+    if (!phase_ms) return;
+    cudaEventRecord(ev[1], st);
+    cudaEventSynchronize(ev[1]);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    phase_ms[which] += ms;
+  };
 #define BCHOL_CK(call)              \
   do {                              \
     e = (call);                     \
     if (e != cudaSuccess) return BCHOL_ERR_CUDA; \
   } while (0)
-  // equilibrate and factor
-  equil_scale_kernel<<<gn, T, 0, st>>>(ab, ldab, n, s);
-  const long long nb = (long long)(k + 1) * n;
-  equil_copy_kernel<<<(unsigned)((nb + T - 1) / T), T, 0, st>>>(ab, ldab, n, k, s, F, ldf);
-  BCHOL_CK(cudaGetLastError());
-  launches += 2;
-  BCHOL_CK(launch_factor(P, F, ldf, info_dev, fws, status, wait_ns, ctas_per_sm, -1, -1, st));
-  launches += 1;
-  int info = 0;
-  BCHOL_CK(cudaMemcpyAsync(&info, info_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
-  BCHOL_CK(cudaStreamSynchronize(st));
-  if (info != 0) {
-    *launches_out = launches;
-    return BCHOL_ERR_NOT_SPD;
-  }
   // ||b||^2 and x_0 = S F^{-1} S b
+  tic();
   BCHOL_CK(cudaMemsetAsync(nrm, 0, sizeof(double) * 4 * nrhs, st));
   for (int c = 0; c < nrhs; ++c) colnorm_kernel<<<gn, T, 0, st>>>(b, ldb, n, c, nrm);
   BCHOL_CK(cudaMemcpy2DAsync(x, sizeof(double) * ldx, b, sizeof(double) * ldb, sizeof(double) * n, nrhs,
                              cudaMemcpyDeviceToDevice, st));
   const unsigned gx = (unsigned)(((long long)n * nrhs + T - 1) / T);
-  scale_rows_kernel<<<gx, T, 0, st>>>(x, ldx, n, nrhs, s);
+  scale_rows_kernel<<<gx, T, 0, st>>>(x, ldx, n, nrhs, m.s);
   int l2 = 0;
-  BCHOL_CK(launch_solve_f32(n, k, nrhs, F, ldf, x, ldx, sws, &l2, st));
-  scale_rows_kernel<<<gx, T, 0, st>>>(x, ldx, n, nrhs, s);
+  BCHOL_CK(launch_solve_f32(n, k, nrhs, m.F, ldf, x, ldx, m.sws, &l2, st));
+  scale_rows_kernel<<<gx, T, 0, st>>>(x, ldx, n, nrhs, m.s);
   BCHOL_CK(cudaGetLastError());
   launches += nrhs + 2 + l2;
+  toc(0);
   // Refinement: r = b - A x (FP64); stop when max_c ||r_c|| / ||b_c|| <= tol, when the
   // residual stops shrinking, or after max_iter corrections d = S F^{-1} S r, x += d.
   double corr = 0.0, res = 0.0, prev = 1e300;
   int it = 0;
   while (true) {
+    tic();
     BCHOL_CK(cudaMemsetAsync(nrm + nrhs, 0, sizeof(double) * 3 * nrhs, st));
     for (int c0 = 0; c0 < nrhs; c0 += kResRhs) {
       const int nr = std::min(kResRhs, nrhs - c0);
@@ -216,30 +265,57 @@ int mixed_solve(int n, int k, int nrhs, const double* ab, long long ldab, const 
     BCHOL_CK(cudaGetLastError());
     BCHOL_CK(cudaMemcpyAsync(h.data(), nrm, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, st));
     BCHOL_CK(cudaStreamSynchronize(st));
+    toc(1);
     res = 0.0;
     for (int c = 0; c < nrhs; ++c) res = std::max(res, std::sqrt(h[nrhs + c] / std::max(h[c], 1e-300)));
     if (!(res > tol) || it >= max_iter || res > 0.5 * prev) break;
     prev = res;
-    scale_rows_kernel<<<gx, T, 0, st>>>(R, n, n, nrhs, s);
-    BCHOL_CK(launch_solve_f32(n, k, nrhs, F, ldf, R, n, sws, &l2, st));
-    scale_rows_kernel<<<gx, T, 0, st>>>(R, n, n, nrhs, s);
+    tic();
+    scale_rows_kernel<<<gx, T, 0, st>>>(R, n, n, nrhs, m.s);
+    BCHOL_CK(launch_solve_f32(n, k, nrhs, m.F, ldf, R, n, m.sws, &l2, st));
+    scale_rows_kernel<<<gx, T, 0, st>>>(R, n, n, nrhs, m.s);
     for (int c = 0; c < nrhs; ++c) update_kernel<<<gn, T, 0, st>>>(x, ldx, R, n, n, c, nrm + 2 * nrhs, nrm + 3 * nrhs);
     BCHOL_CK(cudaGetLastError());
     launches += 2 + l2 + nrhs;
     BCHOL_CK(cudaMemcpyAsync(h.data() + 2 * nrhs, nrm + 2 * nrhs, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost,
                              st));
     BCHOL_CK(cudaStreamSynchronize(st));
+    toc(0);
     corr = 0.0;
     for (int c = 0; c < nrhs; ++c)
       corr = std::max(corr, std::sqrt(h[2 * nrhs + c] / std::max(h[3 * nrhs + c], 1e-300)));
     ++it;
   }
 #undef BCHOL_CK
+  if (phase_ms)
+    for (auto& v : ev) cudaEventDestroy(v);
   *iters_out = it;
   *resid_out = res;
   *corr_out = corr;
   *launches_out = launches;
   return BCHOL_OK;
+}
+
+// The whole mixed solve (bchol_solve_mixed): factor, check info, refine.
+int mixed_solve(int n, int k, int nrhs, const double* ab, long long ldab, const double* b, long long ldb, double* x,
+                long long ldx, int max_iter, double tol, int* info_dev, int tile, int ctas_per_sm, void* wsp,
+                int* status, uint64_t wait_ns, cudaStream_t st, int* iters_out, double* resid_out,
+                double* corr_out, int* launches_out) {
+  int l1 = 0, l2 = 0;
+  int r = mixed_factor(n, k, ab, ldab, info_dev, tile, ctas_per_sm, wsp, nrhs, status, wait_ns, st, &l1);
+  if (r != BCHOL_OK) return r;
+  int info = 0;
+  if (cudaMemcpyAsync(&info, info_dev, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return BCHOL_ERR_CUDA;
+  if (info != 0) {
+    *launches_out = l1;
+    return BCHOL_ERR_NOT_SPD;
+  }
+  r = mixed_refine(n, k, nrhs, ab, ldab, b, ldb, x, ldx, max_iter, tol, tile, wsp, nrhs, st, iters_out, resid_out,
+                   corr_out, &l2, nullptr);
+  *launches_out = l1 + l2;
+  return r;
 }
 
 }  // namespace bchol

@@ -16,13 +16,28 @@
 
 namespace bchol {
 
-enum TaskType { kPotrf = 0, kTrsm = 1, kUpd = 2 };
+enum TaskType { kPotrf = 0, kTrsm = 1, kUpd = 2, kStrip = 3 };
 
 struct Schedule {
   int S, p;
   long long Sreg;   // leading blocks with m_s = m_{s+1} = p
   long long Treg;   // tasks in such a block: 2p + 1 + p(p-1)/2
+  int H = 1;        // chain orders: the updates of a block column go in strips of H tiles (1: one tile each)
 };
+
+// Strips of H consecutive tiles (the last one shorter) that cover cnt tiles of one block column.
+__host__ __device__ inline long long strips_of(long long cnt, int H) { return cnt > 0 ? (cnt + H - 1) / H : 0; }
+// sum_{c=1..N} strips_of(c, H): the strips of the columns with 1, 2, ..., N tiles.
+__host__ __device__ inline long long strips_upto(long long N, int H) {
+  if (N <= 0) return 0;
+  const long long q = N / H, r = N % H;
+  return (long long)H * q * (q + 1) / 2 + r * (q + 1);
+}
+// Rows of the strip that starts at tile row I0 in a block column of step s (its last row is s + m_s).
+__host__ __device__ inline int strip_rows(int H, int s, int ms, int I0) {
+  const int left = s + ms - I0 + 1;
+  return left < H ? left : H;
+}
 
 __host__ __device__ inline int sched_m(const Schedule& a, int s) { return (a.p < a.S - 1 - s) ? a.p : a.S - 1 - s; }
 
@@ -114,7 +129,14 @@ __host__ __device__ inline void decode_task(const Schedule& a, long long t, int&
 // finished in blocks up to s-1, and the tickets of block s read DIAG(s+1) at
 // most.  Regular blocks (m_s = m_{s+1} = p) hold 2(p-1) + p(p-1)/2 tickets.
 
-__host__ __device__ inline long long cp_treg(int p) { return p >= 1 ? 2LL * (p - 1) + (long long)p * (p - 1) / 2 : 0; }
+// With strips of H tiles (H > 1) the updates UPD(I, J, s) of near'(s) and of
+// each column of far(s) are grouped into STRIP(I0, J, s) tasks, I = I0 ..
+// I0+H-1 (cut at s + m_s), at the place of their first tile; the combined order
+// keeps every dependency (a strip comes after the tasks its tiles read, and
+// before every task that reads them).
+__host__ __device__ inline long long cp_treg(int p, int H = 1) {
+  return p >= 1 ? strips_of(p - 1, H) + (p - 1) + strips_upto(p - 1, H) : 0;
+}
 
 __host__ __device__ inline long long cp_panel0(const Schedule& a) {
   const int m0 = sched_m(a, 0);
@@ -123,7 +145,7 @@ __host__ __device__ inline long long cp_panel0(const Schedule& a) {
 
 __host__ __device__ inline long long cp_block_size(const Schedule& a, int s) {
   const long long ms = sched_m(a, s);
-  long long size = (ms > 1 ? ms - 1 : 0) + ms * (ms - 1) / 2;
+  long long size = strips_of(ms - 1, a.H) + strips_upto(ms - 1, a.H);
   if (s + 1 < a.S) {
     const long long m1 = sched_m(a, s + 1);
     size += m1 > 1 ? m1 - 1 : 0;
@@ -156,11 +178,13 @@ __host__ __device__ inline void decode_cp_ticket(const Schedule& a, long long t,
     }
   }
   const int ms = sched_m(a, s);
-  const long long nnear = ms > 1 ? ms - 1 : 0;
+  const int H = a.H;
+  const int tu = H > 1 ? kStrip : kUpd;
+  const long long nnear = strips_of(ms - 1, H);
   if (t < nnear) {  // near'(s)
-    type = kUpd;
+    type = tu;
     J = s + 1;
-    I = s + 2 + (int)t;
+    I = s + 2 + (int)t * H;
     return;
   }
   t -= nnear;
@@ -176,12 +200,12 @@ __host__ __device__ inline void decode_cp_ticket(const Schedule& a, long long t,
     }
     t -= npan;
   }
-  type = kUpd;  // far(s)
+  type = tu;  // far(s)
   J = s + 2;
   while (true) {
-    const long long cnt = s + ms - J + 1;
+    const long long cnt = strips_of(s + ms - J + 1, H);
     if (t < cnt) {
-      I = J + (int)t;
+      I = J + (int)t * H;
       return;
     }
     t -= cnt;
@@ -209,8 +233,8 @@ __host__ __device__ inline void decode_cp_ticket(const Schedule& a, long long t,
 // reads H(s+2) (L(s+2, s)) and DIAG(s+1) at most; DIAG(s) reads H(s).
 // Regular blocks hold 2(p-2) + p(p-1)/2 - 1 tickets.
 
-__host__ __device__ inline long long hp_treg(int p) {
-  return p >= 2 ? 2LL * (p - 2) + (long long)p * (p - 1) / 2 - 1 : 0;
+__host__ __device__ inline long long hp_treg(int p, int H = 1) {
+  return p >= 2 ? 2 * strips_of(p - 2, H) + (p - 2) + strips_upto(p - 2, H) : 0;
 }
 
 __host__ __device__ inline long long hp_panel0(const Schedule& a) {
@@ -220,7 +244,7 @@ __host__ __device__ inline long long hp_panel0(const Schedule& a) {
 
 __host__ __device__ inline long long hp_block_size(const Schedule& a, int s) {
   const long long ms = sched_m(a, s);
-  long long size = (ms > 2 ? ms - 2 : 0) + ms * (ms - 1) / 2 - (ms >= 2 ? 1 : 0);
+  long long size = 2 * strips_of(ms - 2, a.H) + strips_upto(ms - 2, a.H);
   if (s + 1 < a.S) {
     const long long m1 = sched_m(a, s + 1);
     size += m1 > 2 ? m1 - 2 : 0;
@@ -253,11 +277,13 @@ __host__ __device__ inline void decode_hp_ticket(const Schedule& a, long long t,
     }
   }
   const int ms = sched_m(a, s);
-  const long long nnear = ms > 2 ? ms - 2 : 0;
+  const int H = a.H;
+  const int tu = H > 1 ? kStrip : kUpd;
+  const long long nnear = strips_of(ms - 2, H);
   if (t < nnear) {  // near''(s)
-    type = kUpd;
+    type = tu;
     J = s + 1;
-    I = s + 3 + (int)t;
+    I = s + 3 + (int)t * H;
     return;
   }
   t -= nnear;
@@ -273,18 +299,18 @@ __host__ __device__ inline void decode_hp_ticket(const Schedule& a, long long t,
     }
     t -= npan;
   }
-  type = kUpd;  // far'(s): column s+2 from row s+3, then columns s+3.. in full
+  type = tu;  // far'(s): column s+2 from row s+3, then columns s+3.. in full
   J = s + 2;
-  const long long first = ms > 2 ? ms - 2 : 0;
+  const long long first = strips_of(ms - 2, H);
   if (t < first) {
-    I = s + 3 + (int)t;
+    I = s + 3 + (int)t * H;
     return;
   }
   t -= first;
   for (J = s + 3; J <= s + ms; ++J) {
-    const long long cnt = s + ms - J + 1;
+    const long long cnt = strips_of(s + ms - J + 1, H);
     if (t < cnt) {
-      I = J + (int)t;
+      I = J + (int)t * H;
       return;
     }
     t -= cnt;

@@ -1,0 +1,57 @@
+// strip_task.cuh -- the trailing update of the FP64_SPLIT factorization:
+// STRIP(I0, J, s) applies UPD(I, J, s), A_IJ -= L_Is L_Js^T (Algorithm 1), to
+// the h tiles I = I0 .. I0+h-1 of block column J (tiles of b = 16 or 32,
+// h <= 128 / b) as one split product on the tensor cores (split_update.cuh):
+// the h panel tiles L_Is are the b h rows of A, L_Js the b rows of B and the
+// strip of A_IJ is C.  The
+// ready-counter protocol is the per-tile one of factor.cu: the strip waits for
+// each tile's previous update and its panel tiles, and releases each tile's
+// counter after its stores.
+#pragma once
+#include "factor_tasks.cuh"
+#include "split_update.cuh"
+
+namespace bchol {
+
+template <int B>
+__device__ bool task_strip(const FactorArgs& a, int I0, int J, int s, split::Smem<B>& sm, split::Ctx& cx,
+                           int* s_flag) {
+  const int ms = min(a.p, a.S - 1 - s);
+  const int h = strip_rows(a.H, s, ms, I0);
+  if (threadIdx.x == 0) {
+    bool ok = true;
+    for (int t = 0; t < h && ok; ++t) {
+      const int I = I0 + t, s0 = first_step(a, I);
+      ok = wait_tile(a, I, s, s - s0 + 1) && wait_tile(a, I, J, s - s0);
+    }
+    // L_Js is one of the strip's own panel tiles when the strip starts on the diagonal
+    if (ok && !(J >= I0 && J < I0 + h)) ok = wait_tile(a, J, s, s - first_step(a, J) + 1);
+    *s_flag = ok;
+  }
+  __syncthreads();
+  if (!*s_flag) return false;
+  const int rows = B * h;
+  auto band = [&](int gi, int gj) -> double {
+    const int d = gi - gj;
+    return (gi < a.n && d >= 0 && d <= a.k) ? __ldcg(a.ab + d + (long long)gj * a.ldab) : 0.0;
+  };
+  auto la = [&](int r, int k) { return r < rows ? band(I0 * B + r, s * B + k) : 0.0; };
+  auto lb = [&](int j, int k) { return band(J * B + j, s * B + k); };
+  auto ldc = [&](int r, int j) { return r < rows ? band(I0 * B + r, J * B + j) : 0.0; };
+  auto stc = [&](int r, int j, double v) {
+    const int gi = I0 * B + r, gj = J * B + j, d = gi - gj;
+    if (r < rows && gi < a.n && d >= 0 && d <= a.k) a.ab[d + (long long)gj * a.ldab] = v;
+  };
+  if (!split::product<B>(sm, cx, la, lb, ldc, stc, a.wait_ns, a.status, &a.ctl->abort)) return false;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    for (int t = 0; t < h; ++t) {
+      const int I = I0 + t;
+      st_release(&a.flags[fidx(a, I, J)], s - first_step(a, I) + 1);
+    }
+  }
+  return true;
+}
+
+}  // namespace bchol

@@ -32,3 +32,22 @@ def test_argument_errors_need_no_gpu():
     assert lib.bchol_set_wait_limit_ms(h, 0) == -1
     assert lib.bchol_workspace_size(h, 100000, 2000) > 0
     assert lib.bchol_destroy(h) == 0
+
+
+def test_noalloc_size_check_at_n_1e5():
+    """bchol_factor_noalloc's size check runs on the host before any CUDA call: at n = 1e5
+    (tiles of 32 above k = 640) k = 2625 needs 3125 * 84 ready flags, more than its 1 MiB
+    array holds, and is refused; k = 2624 (3125 * 83 flags) passes the check and, with no
+    GPU here, fails only at its first CUDA call."""
+    import pytest
+    import torch
+    lib = bchol.load_library()
+    fn = lib.bchol_factor_noalloc
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                   ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    p = ctypes.c_void_p(256)     # never dereferenced
+    assert fn(None, 100000, 2625, p, 2626, p, p) == 5          # BCHOL_ERR_UNSUPPORTED
+    if torch.cuda.is_available():
+        pytest.skip("the accepted size would launch on the GPU with placeholder pointers")
+    assert fn(None, 100000, 2624, p, 2625, p, p) == 3          # BCHOL_ERR_CUDA: no device here

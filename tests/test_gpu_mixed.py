@@ -47,3 +47,57 @@ def test_mixed_reports_not_spd():
     b = torch.ones(n, dtype=torch.float64, device="cuda")
     x, info, iters, resid, corr = solve_mixed(ab, k, b)
     assert int(info.item()) == 501
+
+
+# ------------------------------------------------- the FP32_UPDATE precision mode of bchol_factor / bchol_solve
+@pytest.mark.parametrize("n,k,nrhs,diag", [(3000, 200, 1, "log1e3"), (5000, 700, 20, "log1e3"), (2000, 50, 3, "u15"),
+                                           (1000, 40, 17, "dd"), (64, 100, 1, "log1e3")])
+def test_fp32_update_mode_reaches_fp64_accuracy(n, k, nrhs, diag):
+    """bchol_set_precision(FP32_UPDATE): bchol_factor factors an equilibrated copy with
+    FP32-accumulated updates and leaves ab holding A; bchol_solve refines in FP64 against
+    A, 16 columns at a time (20 and 17 columns span two groups)."""
+    L0, A, B = g.problem(n, k, seed=13, diag=diag, exact=False, nrhs=nrhs)
+    h = bchol.Handle()
+    h.set_precision(bchol.FP32_UPDATE, max_refine=20, tol=1e-13)
+    ab = bchol.band_from_numpy(A)
+    ab_copy = ab.clone()
+    b = _rhs_gpu(B)
+    info = bchol.factor(ab, k, handle=h)
+    bchol.solve(ab, k, b, handle=h)
+    rc, infos = bchol.get_info(info, handle=h)
+    assert rc == 0 and infos == [0]
+    assert torch.equal(ab, ab_copy)                      # A is kept for the refinement
+    iters, resid, corr = h.last_refinement()
+    X = b.T.contiguous().cpu().numpy().T
+    Lref, _ = oracle.pbtrf(A, k)
+    Xref = oracle.pbtrs(Lref, k, B)
+    err = np.linalg.norm(X - Xref, axis=0) / np.linalg.norm(Xref, axis=0)
+    print(f"FP32_UPDATE n={n} k={k} nrhs={nrhs} {diag}: iters {iters}, resid {resid:.2e}, "
+          f"max rel err vs FP64 oracle {err.max():.2e}")
+    assert err.max() <= 1e-10 and resid <= 1e-12
+
+
+def test_fp32_update_mode_checks_its_factorization():
+    n, k = 900, 30
+    _, A, B = g.problem(n, k, seed=3, diag="log1e3", exact=False, nrhs=1)
+    h = bchol.Handle()
+    h.set_precision(bchol.FP32_UPDATE)
+    ab = bchol.band_from_numpy(A)
+    b = _rhs_gpu(B)
+    with pytest.raises(bchol.BcholError) as e:           # no factorization on this handle yet
+        bchol.solve(ab, k, b, handle=h)
+    assert e.value.code == -1
+    bchol.factor(ab, k, handle=h)
+    other = ab.clone()
+    with pytest.raises(bchol.BcholError) as e:           # a different band than the one factored
+        bchol.solve(other, k, b, handle=h)
+    assert e.value.code == -1
+    A2 = g.dd_band(n, k, seed=2)
+    A2[0, 300] = -1.0e4
+    ab2 = bchol.band_from_numpy(A2)
+    info = bchol.factor(ab2, k, handle=h)
+    with pytest.raises(bchol.BcholError) as e:           # the factorization failed: not SPD
+        bchol.solve(ab2, k, b, handle=h)
+    assert e.value.code == 1
+    rc, infos = bchol.get_info(info, handle=h)
+    assert rc == 1 and infos == [301]

@@ -124,3 +124,93 @@ def test_launch_cannot_deadlock(n, k, b, workers):
                 ai[r] += 1
                 progress = True
         assert progress, f"stalled with {len(done)} of {len(order)} tasks done"
+
+
+def _expand(task, S, p, H):
+    """The per-tile tasks a task stands for: a strip (type 3) of block column J at
+    step s is the updates UPD(I, J, s) of its tiles I = I0 .. min(I0+H-1, s+m_s)."""
+    typ, s, I, J = task
+    if typ != 3:
+        return [task]
+    ms = min(p, S - 1 - s)
+    return [(2, s, r, J) for r in range(I, min(I + H - 1, s + ms) + 1)]
+
+
+SPLIT = 3   # BCHOL_FP64_SPLIT
+
+
+@pytest.mark.parametrize("b", [16, 32])
+@pytest.mark.parametrize("n,k", [(100, 31), (100, 32), (3000, 130), (640, 200), (2000, 1000), (4000, 2000),
+                                 (700, 300), (1300, 1290), (64, 63), (33, 32), (5000, 700), (200, 17)])
+def test_split_strips_cover_every_update_once_in_order(n, k, b):
+    """With tiles of 16 or 32 and the split precision mode, the updates of each block column run
+    as strips of up to 128 / b tiles; expanded into tiles, the order holds every task of
+    Algorithm 1 exactly once, and every tile task comes after the tasks it depends on."""
+    H = 128 // b
+    got = bchol.plan_tasks(n, k, b, precision=SPLIT)
+    want, S, p = expected_tasks(n, k, b)
+    if p >= 3:                         # (with p = 2 the helper CTAs take every update outside the chain)
+        assert any(t[0] == 3 for t in got)
+    flat = [u for t in got for u in _expand(t, S, p, H)]
+    assert len(flat) == len(set(flat)) == len(want)
+    assert set(flat) == want
+    pos = {}
+    for i, t in enumerate(got):
+        for u in _expand(t, S, p, H):
+            pos[u] = i
+    for i, t in enumerate(got):
+        for u in _expand(t, S, p, H):
+            for d in _deps(u, p):
+                if d in _expand(t, S, p, H):
+                    continue          # a strip's own tiles: L_Js of a strip that starts on the diagonal
+                assert pos[d] < i, (d, t)
+    # the other precision modes keep one task per tile
+    assert bchol.plan_tasks(n, k, b) == bchol.plan_tasks(n, k, b, precision=0)
+    assert all(t[0] != 3 for t in bchol.plan_tasks(n, k, 64, precision=SPLIT))
+
+
+@pytest.mark.parametrize("workers", [1, 3, 7])
+@pytest.mark.parametrize("n,k,b", [(3000, 130, 32), (2000, 1000, 32), (4000, 2000, 32), (700, 300, 32),
+                                   (1300, 1290, 32), (3000, 130, 16), (2000, 700, 16), (1000, 50, 16)])
+def test_split_launch_cannot_deadlock(n, k, b, workers):
+    """The launch simulation of test_launch_cannot_deadlock with strip tasks: a strip runs once
+    every task its tiles read is done (its own tiles excepted)."""
+    H = 128 // b
+    order = bchol.plan_tasks(n, k, b, precision=SPLIT)
+    kk = min(k, n - 1)
+    S = math.ceil(n / b)
+    p = min(math.ceil(kk / b), S - 1)
+    helpers = p >= 2                   # the split mode runs the helper CTAs at every p >= 2
+
+    def deps(t):
+        own = set(_expand(t, S, p, H))
+        return [d for u in own for d in _deps(u, p) if d not in own]
+
+    chain = [t for t in order if t[0] != 3 and _is_chain(t)]
+    agents = [[t for t in order if t[0] != 3 and helpers and _helper(t) == r] for r in (1, 2)]
+    tickets = [t for t in order if t[0] == 3 or not (_is_chain(t) or (helpers and _helper(t)))]
+    assert len(chain) + sum(map(len, agents)) + len(tickets) == len(order)
+    done = set()
+    ai = [0, 0]
+    ci, next_ticket = 0, 0
+    held = [[] for _ in range(workers)]
+    total = sum(len(_expand(t, S, p, H)) for t in order)
+    while len(done) < total:
+        progress = False
+        for w in range(workers):
+            while len(held[w]) < 2 and next_ticket < len(tickets):
+                held[w].append(tickets[next_ticket])
+                next_ticket += 1
+            if held[w] and all(d in done for d in deps(held[w][0])):
+                done.update(_expand(held[w].pop(0), S, p, H))
+                progress = True
+        if ci < len(chain) and all(d in done for d in deps(chain[ci])):
+            done.add(chain[ci])
+            ci += 1
+            progress = True
+        for r in range(2):
+            if ai[r] < len(agents[r]) and all(d in done for d in deps(agents[r][ai[r]])):
+                done.add(agents[r][ai[r]])
+                ai[r] += 1
+                progress = True
+        assert progress, f"stalled with {len(done)} of {total} tile tasks done"

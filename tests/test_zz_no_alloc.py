@@ -5,7 +5,8 @@ memory, real-time hosts that forbid allocation after start-up, plugins whose
 host application owns every allocation) cannot let the library call
 cudaMalloc.  This entry point keeps its scratch in a fixed array inside the
 library.  The test calls it through the C ABI and compares its factor with the
-one bchol_factor produces, on two calls in a row.  This file is collected
+one bchol_factor produces (the same kernel with the same settings, so the same
+bits) and with the CPU oracle, on two calls in a row.  This file is collected
 last so that a run that stops at the first failure has run every other test.
 """
 import ctypes
@@ -15,6 +16,7 @@ import pytest
 import torch
 
 import bandgen as g
+import oracle
 import paper_2305_04635_gb300 as bchol
 
 pytestmark = pytest.mark.gpu
@@ -65,8 +67,11 @@ def test_noalloc_factor_matches_bchol_factor_twice():
         L, info, status = _factor_noalloc(fn, A, k)
         assert info == 0 and status == 0
         err = np.linalg.norm(L - L_ref) / np.linalg.norm(L_ref)
-        print(f"n={n} k={k}: relative difference to bchol_factor {err:.2e}")
-        assert err <= TOL_L
+        L_or, iref = oracle.pbtrf(A, k)
+        err_or = np.linalg.norm(L - L_or) / np.linalg.norm(L_or)
+        print(f"n={n} k={k}: relative difference to bchol_factor {err:.2e}, to the oracle {err_or:.2e}")
+        assert err == 0.0
+        assert iref == 0 and err_or <= TOL_L
 
 
 def test_noalloc_rejects_problems_beyond_its_scratch():
@@ -74,3 +79,17 @@ def test_noalloc_rejects_problems_beyond_its_scratch():
     # 1e7 rows with k = 1000 need about 10 million ready flags, far past the fixed array.
     rc = fn(None, 10_000_000, 1000, ctypes.c_void_p(256), 1001, ctypes.c_void_p(256), ctypes.c_void_p(256))
     assert rc == 5   # BCHOL_ERR_UNSUPPORTED, nothing launched
+
+
+def test_noalloc_size_limit_at_its_edge():
+    """n = 1e6 with tiles of 16: k = 48 needs 62500 * 4 ready flags (1000256 bytes with the
+    control block, just under 1 MiB) and runs, with the bits of bchol_factor; k = 49 needs
+    62500 * 5 and is refused before anything is launched."""
+    fn = _noalloc_fn()
+    n, k = 1_000_000, 48
+    _, A, _ = g.problem(n, k, seed=9, diag="u15", exact=True)
+    L, info, status = _factor_noalloc(fn, A, k)
+    assert info == 0 and status == 0
+    assert np.array_equal(L, _factor_plain(A, k))
+    rc = fn(None, n, k + 1, ctypes.c_void_p(256), k + 2, ctypes.c_void_p(256), ctypes.c_void_p(256))
+    assert rc == 5
