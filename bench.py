@@ -52,10 +52,50 @@ FP64_PEAK_TFLOPS = 1.25
 HBM_FALLBACK_GBS = 6800.0
 L2_FLUSH_BYTES = 256 << 20
 PRECISIONS = {"fp64": 0, "split": 3}
+# bf16 MACs per FP64 multiply-add in the split updates: the 28 digit pairs (a + b <= 6) of two
+# seven-digit operands.
+SPLIT_MACS_PER_FMA = 28
 # DRAM bytes (read + write) of one factor launch at n = 20000 for each sweep k, from
 # an ncu capture of dram__bytes_read.sum + dram__bytes_write.sum of this kernel;
 # traffic is proportional to n at fixed k, so it is scaled by n / 20000.
 TRAFFIC_N20000 = {50: 8.5e6, 100: 16.8e6, 200: 35.6e6, 500: 105.7e6, 1000: 258.1e6, 2000: 569.3e6}
+
+
+def measured_bf16_tflops() -> tuple[float, str]:
+    """Sustained cuBLAS bf16 rate (the split updates run inside a long step), else the fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["bf16_tflops_sustained"]), "measured"
+    except Exception:
+        return 1700.0, "fallback"
+
+
+def host_cpu() -> dict:
+    """Model name and logical core count of the host (for the CPU baseline's context)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                low = line.lower()
+                if low.startswith("model name") or low.startswith("cpu model") or low.startswith("hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=5).stdout
+            for line in out.splitlines():
+                if line.startswith("Model name") or line.startswith("Vendor ID"):
+                    model = line.split(":", 1)[1].strip()
+                    if line.startswith("Model name"):
+                        break
+        except Exception:
+            pass
+    import platform
+    return {"cpu_model": model or platform.processor() or platform.machine(), "nproc": os.cpu_count(),
+            "machine": platform.machine()}
 
 
 def measured_hbm_gbs() -> tuple[float, str]:
@@ -154,6 +194,8 @@ def run_ours(args, rank: int, world: int, dev: int):
                        device="cuda"), host_A=host_A, host_b=host_b, host_x=host_x, host_info=host_info)
     flush = torch.empty(L2_FLUSH_BYTES // 8, dtype=torch.float64, device="cuda")
     ev = {k: [torch.cuda.Event(enable_timing=True) for _ in range(3)] for k in ks}
+    # Which matrices run the split updates (the library's rule for the automatic tile).
+    split_k = {k: args.precision == "split" and (args.tile == 32 or (args.tile == 0 and k > 640)) for k in ks}
     fac_ms = {k: [] for k in ks}
     sol_ms = {k: [] for k in ks}
 
@@ -235,6 +277,28 @@ def run_ours(args, rank: int, world: int, dev: int):
             raise RuntimeError(f"e2e factorization failed for k={k}")
     wall_e2e = te1 - te0
 
+    # The same factorizations with FP64-FMA updates, for the matrices that ran the split updates
+    # (outside the timed regions).
+    fma_ms = {}
+    if any(split_k.values()):
+        h64 = bchol.Handle(tile=args.tile)
+        for k in ks:
+            if not split_k[k]:
+                continue
+            bb = bufs[k]
+            times = []
+            for _ in range(3):
+                bb["work"].copy_(bb["pristine"])
+                flush.fill_(1.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                bchol.factor(bb["work"], k, info=bb["info"], handle=h64)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            fma_ms[k] = statistics.median(times[1:])
+        del h64
+
     walls = gather_max(world, [wall, wall_e2e])
     wall, wall_e2e = walls
     F = sum(flops_eq1(n, k) for k in ks)
@@ -242,6 +306,7 @@ def run_ours(args, rank: int, world: int, dev: int):
     e2e_value = job_rate(world, F, args.steps, wall_e2e)
 
     hbm, hbm_kind = measured_hbm_gbs()
+    bf16, bf16_kind = measured_bf16_tflops()
     per_k = {}
     tot_flop, tot_ms = 0.0, 0.0
     for k in ks:
@@ -253,7 +318,16 @@ def run_ours(args, rank: int, world: int, dev: int):
                          "factor_gflops_nk2": round(flops_nk2(n, k) / fm / 1e6, 2),
                          "frac_fp64_roofline": round(roof / fm, 4),
                          "dram_bytes": (round(TRAFFIC_N20000[k] * n / 20000) if k in TRAFFIC_N20000 else None),
-                         "algorithmic_bytes": 16 * (k + 1) * n}
+                         "algorithmic_bytes": 16 * (k + 1) * n,
+                         "updates": "split" if split_k[k] else "fp64_fma",
+                         # the solve reads the band twice: 16 (k+1) n bytes against the measured HBM copy rate
+                         "solve_frac_hbm": round(16 * (k + 1) * n / (hbm * 1e9) * 1e3 / sm, 4)}
+        if split_k[k]:
+            per_k[str(k)]["factor_ms_fp64_fma"] = round(fma_ms[k], 4)
+            per_k[str(k)]["split_speedup"] = round(fma_ms[k] / fm, 3)
+            # the split updates' own roofline: 28 bf16 MACs per FP64 FMA of n k^2, against sustained bf16
+            per_k[str(k)]["split_tensor_frac"] = round(2 * SPLIT_MACS_PER_FMA * flops_nk2(n, k) / 2 / (fm * 1e-3)
+                                                       / (bf16 * 1e12), 4)
         tot_flop += flops_nk2(n, k) * len(fac_ms[k])
         tot_ms += sum(fac_ms[k])
     achieved_tflops = tot_flop / (tot_ms * 1e-3) / 1e12
@@ -265,6 +339,9 @@ def run_ours(args, rank: int, world: int, dev: int):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"plain FP64 sweep: n={n}, k in {ks}, L0 diag log-uniform [1,1e3], 1 RHS, "
                                "factor + solve per matrix", "n": n, "k": ks, "nrhs": 1,
+                   "precision": args.precision,
+                   "updates": ("k > 640: FP64-accurate split bf16 products on the tensor cores (tile 32); "
+                               "k <= 640: FP64 FMA (tile 16)") if args.precision == "split" else "FP64 FMA",
                    "l2": "256 MB flush write before every factorization (inputs for k <= 100 are below L2 size)",
                    "parallelism": f"replicas x{world}"},
         "per_k": per_k,
@@ -278,7 +355,11 @@ def run_ours(args, rank: int, world: int, dev: int):
                      "traffic_note": "DRAM bytes per factor launch, mean over the sweep's launches (ncu capture at "
                                      "n = 20000, scaled by n); per-k figures in per_k",
                      "kernel": "factor_kernel", "flops_per_launch": "n*k^2",
-                     "peak_source": "FP64 nominal from unit counts and clock (alu)"},
+                     "peak_source": "FP64 nominal from unit counts and clock (alu)",
+                     "note": ("achieved counts n*k^2 FP64 multiply-adds as 2 flops each; the k > 640 launches run "
+                              "them as split bf16 products on the tensor cores, so their share can pass the FP64 "
+                              "ceiling; per_k[k].split_tensor_frac is their tensor-core fraction "
+                              f"(bf16 sustained {bf16} TFLOP/s, {bf16_kind})") if any(split_k.values()) else None},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
     }
@@ -369,11 +450,28 @@ def next_batched(count: int = 512, reps: int = 3) -> dict:
         raise RuntimeError("batched leg: a batched factorization failed")
     diff = max(float(torch.linalg.norm(a - c) / torch.linalg.norm(c)) for a, c in zip(bw, x_plain))
     batch.close()
+    # the factorizations alone (a batch without right-hand sides), for the factor / solve split
+    fbatch = bchol.Batch(work, ks, None, tile=tile, ctas_per_sm=cps)
+    ftimes = []
+    for _ in range(reps + 1):
+        restore()
+        e0, e1 = _ev()
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            fbatch.run(h)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ftimes.append(e0.elapsed_time(e1))
+    factor_ms = statistics.median(ftimes[1:])
+    fbatch.close()
+    nk2 = sum(flops_nk2(n, k) for n, k in zip(ns, ks))
     return {"workload": f"{count} systems, n log-uniform [1e3,5e4], k log-uniform [50,400], 4 RHS, "
                         "L0 diag log-uniform [1,1e3]",
             "flops_eq1": F, "plain_loop_ms": round(plain_ms, 3), "batched_ms": round(batched_ms, 3),
             "speedup_vs_plain": round(plain_ms / batched_ms, 3),
             "batched_gflops_eq1": round(F / batched_ms / 1e6, 2),
+            "batched_factor_ms": round(factor_ms, 3), "batched_solve_ms": round(batched_ms - factor_ms, 3),
+            "factor_frac_fp64_roofline": round(nk2 / (factor_ms * 1e-3) / (FP64_PEAK_TFLOPS * 1e12), 4),
             "factorizations_per_s": round(count / batched_ms * 1e3, 2),
             "plain_factorizations_per_s": round(count / plain_ms * 1e3, 2),
             "tile": tile, "ctas_per_sm": cps, "cuda_graph": True,
@@ -381,49 +479,58 @@ def next_batched(count: int = 512, reps: int = 3) -> dict:
 
 
 def next_mixed(n: int = 200000, k: int = 1000, nrhs: int = 16, tol: float = 1e-10, reps: int = 2) -> dict:
-    """n = 2e5, k = 1000, cond(A) ~ 1e6, 16 RHS: the FP64 factor + solve against the mixed solve
-    (FP32-accumulated trailing updates, FP64 POTRF, FP64 residual refinement to tol)."""
+    """n = 2e5, k = 1000, cond(A) ~ 1e6, 16 RHS: the FP32_UPDATE precision mode through
+    bchol_factor / bchol_solve (FP32-accumulated trailing updates, FP64 POTRF, FP64 residual
+    refinement to tol), against the FP64 factor + solve with FMA updates and with the split
+    (tensor-core) updates.  Each leg is timed with CUDA events, factor and solve apart."""
     import paper_2305_04635_gb300 as bchol
-    from paper_2305_04635_gb300.mixed import solve_mixed
 
     A = bandgen.band_product(bandgen.l0_band(n, k, 0, "log1e3"), k)
     dA = bchol.band_from_numpy(A)
     b0 = _colmajor(bandgen.rhs(n, nrhs, 0))
     del A
-    h = bchol.Handle()
-    fp64 = []
-    for _ in range(reps + 1):
-        ab, b = dA.clone(), b0.clone()
-        torch.cuda.synchronize()
-        e0, e1 = _ev()
-        e0.record()
-        info = bchol.factor(ab, k, handle=h)
-        bchol.solve(ab, k, b, handle=h)
-        e1.record()
-        torch.cuda.synchronize()
-        fp64.append(e0.elapsed_time(e1))
-    x64 = b
-    del ab
-    hm = bchol.Handle()
-    mixed, res = [], None
-    for _ in range(reps + 1):
-        torch.cuda.synchronize()
-        e0, e1 = _ev()
-        e0.record()
-        res = solve_mixed(dA, k, b0, tol=tol, handle=hm)
-        e1.record()
-        torch.cuda.synchronize()
-        mixed.append(e0.elapsed_time(e1))
-    x, minfo, iters, resid, corr = res
-    if int(minfo.item()) != 0 or int(info.item()) != 0:
-        raise RuntimeError("mixed leg: factorization failed")
-    diff = float((torch.linalg.norm(x - x64, dim=0) / torch.linalg.norm(x64, dim=0)).max())
-    fp64_ms, mixed_ms = statistics.median(fp64[1:]), statistics.median(mixed[1:])
+
+    def leg(precision):
+        h = bchol.Handle()
+        h.set_precision(precision, max_refine=10, tol=tol)
+        fac, sol = [], []
+        x = None
+        for _ in range(reps + 1):
+            ab, b = dA.clone(), b0.clone()
+            torch.cuda.synchronize()
+            e0, e1, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True), \
+                torch.cuda.Event(enable_timing=True)
+            e0.record()
+            info = bchol.factor(ab, k, handle=h)
+            e1.record()
+            bchol.solve(ab, k, b, handle=h)
+            e2.record()
+            torch.cuda.synchronize()
+            if int(info.item()) != 0:
+                raise RuntimeError(f"mixed leg: factorization failed (precision {precision})")
+            fac.append(e0.elapsed_time(e1))
+            sol.append(e1.elapsed_time(e2))
+            x = b
+        out = {"factor_ms": round(statistics.median(fac[1:]), 3), "solve_ms": round(statistics.median(sol[1:]), 3)}
+        out["total_ms"] = round(out["factor_ms"] + out["solve_ms"], 3)
+        return out, x, h
+
+    fma, x_fma, _ = leg(bchol.FP64)
+    split, x_split, _ = leg(bchol.FP64_SPLIT)
+    mixed, x_mix, hm = leg(bchol.FP32_UPDATE)
+    iters, resid, corr = hm.last_refinement()
+
+    def rel(x, y):
+        return float((torch.linalg.norm(x - y, dim=0) / torch.linalg.norm(y, dim=0)).max())
+
+    best = min(fma["total_ms"], split["total_ms"])
     return {"workload": f"n={n}, k={k}, L0 diag log-uniform [1,1e3] (cond ~1e6), {nrhs} RHS",
-            "fp64_factor_solve_ms": round(fp64_ms, 3), "mixed_ms": round(mixed_ms, 3),
-            "speedup_vs_fp64": round(fp64_ms / mixed_ms, 3), "refine_tol_rel_residual": tol,
-            "iterations": iters, "final_rel_residual": resid,
-            "max_rel_diff_x_vs_fp64": diff}
+            "mixed": mixed, "fp64_fma": fma, "fp64_split": split,
+            "fp64_factor_solve_ms": fma["total_ms"], "mixed_ms": mixed["total_ms"],
+            "speedup_vs_fp64": round(fma["total_ms"] / mixed["total_ms"], 3),
+            "speedup_vs_best_fp64": round(best / mixed["total_ms"], 3),
+            "refine_tol_rel_residual": tol, "iterations": iters, "final_rel_residual": resid,
+            "max_rel_diff_x_vs_fp64": rel(x_mix, x_fma), "max_rel_diff_split_vs_fma": rel(x_split, x_fma)}
 
 
 def next_adjoint(n: int = 20000, k: int = 200, probe_cols: int = 256, reps: int = 3) -> dict:
@@ -467,9 +574,15 @@ def next_adjoint(n: int = 20000, k: int = 200, probe_cols: int = 256, reps: int 
         raise RuntimeError("adjoint leg: non-finite gradient")
     fw_ms, bw_ms = statistics.median(fw[1:]), statistics.median(bw[1:])
     alt_ms = statistics.median(alt[1:]) * n / probe_cols
+    # The band of A^{-1} by the Takahashi recurrences: k multiply-adds for each of the ~n k band
+    # entries, 2 n k^2 flops (twice the factorization's n k^2).
+    selinv_flops = 2.0 * n * k * k
     return {"workload": f"n={n}, k={k}, loss = 0.5||A^-1 b||^2 + log det A, b ~ N(0,1)",
             "forward_ms": round(fw_ms, 3), "backward_ms": round(bw_ms, 3),
             "backward_over_forward": round(bw_ms / fw_ms, 3),
+            "backward_gflops": round(selinv_flops / bw_ms / 1e6, 2),
+            "backward_frac_fp64_roofline": round(selinv_flops / (bw_ms * 1e-3) / (FP64_PEAK_TFLOPS * 1e12), 4),
+            "backward_flops": "2 n k^2 (band of A^-1 by selected inversion)",
             "alt_inverse_columns_by_solves_ms": round(alt_ms, 3),
             "alt_sample": f"{probe_cols} unit-vector solves, scaled by n/{probe_cols}",
             "speedup_vs_alt": round(alt_ms / bw_ms, 2)}
@@ -498,6 +611,7 @@ def cpu_baseline(n: int, ks: list[int], data=None, budget_s: float = 20.0) -> di
         total_t += dt * scale
         samples.append(f"k={k}: n'={nprime}")
     return {"value": round(total_f / total_t / 1e9, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+            "host": host_cpu(),
             "sample": "factor+solve of the leading n' rows of each matrix, time scaled by F(n,k)/F(n',k): "
                       + ", ".join(samples)}
 
@@ -534,7 +648,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-next", action="store_true", help="skip the batched, mixed and adjoint legs")
     ap.add_argument("--tile", type=int, default=0, help="tile size (0: automatic)")
-    ap.add_argument("--precision", default="fp64", choices=sorted(PRECISIONS),
+    ap.add_argument("--precision", default="split", choices=sorted(PRECISIONS),
                     help="trailing-update arithmetic: FP64 FMA, or FP64-accurate split products on the tensor cores")
     args = ap.parse_args()
 

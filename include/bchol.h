@@ -65,8 +65,11 @@ typedef enum {
  *   BCHOL_TF32_UPDATE  not built; bchol_set_precision returns BCHOL_ERR_UNSUPPORTED.
  *   BCHOL_FP64_SPLIT   FP64-accurate updates from exact bf16 digit products on the
  *                      tensor cores (bchol_check_split_product), with tiles of 16
- *                      and 32; with tiles of 64 the updates are FP64 FMA.  L
- *                      agrees with the FP64 mode to rounding. */
+ *                      and 32; with tiles of 64 the updates are FP64 FMA.  With
+ *                      the automatic tile they run where that tile is 32
+ *                      (k > 640); for smaller k the diagonal chain bounds the
+ *                      factorization and the FP64 updates are kept.  L agrees
+ *                      with the FP64 mode to rounding. */
 typedef enum {
   BCHOL_FP64 = 0,
   BCHOL_FP32_UPDATE = 1,

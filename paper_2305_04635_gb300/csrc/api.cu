@@ -353,7 +353,11 @@ bchol_status_t bchol_factor(bchol_handle_t h, int n, int k, double* ab, int ldab
     h->last_launches = launches;
     return BCHOL_OK;
   }
-  const FactorPlan P = make_factor_plan(n, kk, b, split_mode(h->precision));
+  // With the automatic tile the split updates run where that tile is 32 (k > 640):
+  // below, the diagonal chain bounds the factorization and the FP64 updates of
+  // 16-tiles are faster (measured); a tile set with bchol_set_tile is taken as is.
+  const bool split = split_mode(h->precision) && (h->tile != 0 || b == 32);
+  const FactorPlan P = make_factor_plan(n, kk, b, split);
   cudaError_t e = launch_factor(P, ab, ldab, info_dev, ws + kStatusBytes, status,
                                 (uint64_t)h->wait_ms * 1000000ull, h->ctas_per_sm ? h->ctas_per_sm : auto_ctas_per_sm(kk),
                                 h->stall_I, h->stall_J, h->stream);

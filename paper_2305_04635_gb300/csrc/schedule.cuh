@@ -22,15 +22,21 @@ struct Schedule {
   int S, p;
   long long Sreg;   // leading blocks with m_s = m_{s+1} = p
   long long Treg;   // tasks in such a block: 2p + 1 + p(p-1)/2
-  int H = 1;        // chain orders: the updates of a block column go in strips of H tiles (1: one tile each)
+  int H = 1;        // chain orders: the updates of a block column go in strips of H tiles (1: one tile each; 1, 2, 4 or 8)
 };
 
+// log2 of a strip height (1, 2, 4 or 8): the ticket decode runs on every
+// task's critical path, so strips are counted with shifts, not divisions.
+__host__ __device__ inline int strip_shift(int H) { return H >= 8 ? 3 : H >= 4 ? 2 : H >= 2 ? 1 : 0; }
 // Strips of H consecutive tiles (the last one shorter) that cover cnt tiles of one block column.
-__host__ __device__ inline long long strips_of(long long cnt, int H) { return cnt > 0 ? (cnt + H - 1) / H : 0; }
+__host__ __device__ inline long long strips_of(long long cnt, int H) {
+  return cnt > 0 ? (cnt + H - 1) >> strip_shift(H) : 0;
+}
 // sum_{c=1..N} strips_of(c, H): the strips of the columns with 1, 2, ..., N tiles.
 __host__ __device__ inline long long strips_upto(long long N, int H) {
   if (N <= 0) return 0;
-  const long long q = N / H, r = N % H;
+  const int sh = strip_shift(H);
+  const long long q = N >> sh, r = N & (H - 1);
   return (long long)H * q * (q + 1) / 2 + r * (q + 1);
 }
 // Rows of the strip that starts at tile row I0 in a block column of step s (its last row is s + m_s).
@@ -202,10 +208,11 @@ __host__ __device__ inline void decode_cp_ticket(const Schedule& a, long long t,
   }
   type = tu;  // far(s)
   J = s + 2;
+  const int sh = strip_shift(H);
   while (true) {
-    const long long cnt = strips_of(s + ms - J + 1, H);
+    const long long cnt = ((long long)(s + ms - J + 1) + H - 1) >> sh;
     if (t < cnt) {
-      I = J + (int)t * H;
+      I = J + ((int)t << sh);
       return;
     }
     t -= cnt;
@@ -307,10 +314,11 @@ __host__ __device__ inline void decode_hp_ticket(const Schedule& a, long long t,
     return;
   }
   t -= first;
+  const int sh = strip_shift(H);
   for (J = s + 3; J <= s + ms; ++J) {
-    const long long cnt = strips_of(s + ms - J + 1, H);
+    const long long cnt = ((long long)(s + ms - J + 1) + H - 1) >> sh;
     if (t < cnt) {
-      I = J + (int)t * H;
+      I = J + ((int)t << sh);
       return;
     }
     t -= cnt;

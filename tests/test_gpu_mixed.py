@@ -101,3 +101,33 @@ def test_fp32_update_mode_checks_its_factorization():
     assert e.value.code == 1
     rc, infos = bchol.get_info(info, handle=h)
     assert rc == 1 and infos == [301]
+
+
+def test_fp32_update_mode_at_the_configuration_size():
+    """n = 2e5, k = 1000, L0 diagonal log-uniform in [1, 1e3] (cond(A) ~ 1e6), 16 right-hand
+    sides, refined to a 1e-10 relative residual: the timed mixed-precision configuration.
+    L0 lies on a 2^-12 grid, so the oracle's factor of A is L0 itself (pinned on the CPU) and
+    the oracle's solution is its substitution on L0; two of the 16 columns are compared with
+    it, and every column's residual b - A x is recomputed by the oracle on sampled rows."""
+    n, k, nrhs = 200000, 1000, 16
+    L0, A, B = g.problem(n, k, seed=0, diag="log1e3", exact=True, nrhs=nrhs)
+    h = bchol.Handle()
+    h.set_precision(bchol.FP32_UPDATE, max_refine=10, tol=1e-10)
+    ab = bchol.band_from_numpy(A)
+    b = _rhs_gpu(B)
+    info = bchol.factor(ab, k, handle=h)
+    bchol.solve(ab, k, b, handle=h)
+    rc, infos = bchol.get_info(info, handle=h)
+    assert rc == 0 and infos == [0]
+    iters, resid, corr = h.last_refinement()
+    X = b.T.contiguous().cpu().numpy().T
+    errs = []
+    for c in (0, 11):
+        xref = oracle.pbtrs(L0, k, B[:, c])
+        errs.append(float(np.linalg.norm(X[:, c] - xref) / np.linalg.norm(xref)))
+    rows = np.random.default_rng(5).integers(0, n, 3000)
+    res = max(float(np.abs(oracle.sbmv_residual_sampled(A, k, X[:, c], B[:, c], rows)).max()
+                    / np.abs(B[rows, c]).max()) for c in range(nrhs))
+    print(f"FP32_UPDATE n={n} k={k} nrhs={nrhs}: iters {iters}, resid {resid:.2e}, "
+          f"rel err x vs oracle {max(errs):.2e}, max sampled |b - Ax| / max|b| {res:.2e}")
+    assert resid <= 1e-10 and max(errs) <= 1e-10 and res <= 1e-10
