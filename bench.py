@@ -59,6 +59,12 @@ SPLIT_MACS_PER_FMA = 28
 # an ncu capture of dram__bytes_read.sum + dram__bytes_write.sum of this kernel;
 # traffic is proportional to n at fixed k, so it is scaled by n / 20000.
 TRAFFIC_N20000 = {50: 8.5e6, 100: 16.8e6, 200: 35.6e6, 500: 105.7e6, 1000: 258.1e6, 2000: 569.3e6}
+# The same for the launches with the split tensor-core updates (tile 32).
+TRAFFIC_SPLIT_N20000 = {1000: 256.7e6, 2000: 554.7e6}
+
+
+def traffic_table(split: bool) -> dict:
+    return TRAFFIC_SPLIT_N20000 if split else TRAFFIC_N20000
 
 
 def measured_bf16_tflops() -> tuple[float, str]:
@@ -317,7 +323,8 @@ def run_ours(args, rank: int, world: int, dev: int):
                          "factor_gflops_eq1": round(flops_eq1(n, k) / fm / 1e6, 2),
                          "factor_gflops_nk2": round(flops_nk2(n, k) / fm / 1e6, 2),
                          "frac_fp64_roofline": round(roof / fm, 4),
-                         "dram_bytes": (round(TRAFFIC_N20000[k] * n / 20000) if k in TRAFFIC_N20000 else None),
+                         "dram_bytes": (round(traffic_table(split_k[k])[k] * n / 20000)
+                                        if k in traffic_table(split_k[k]) else None),
                          "algorithmic_bytes": 16 * (k + 1) * n,
                          "updates": "split" if split_k[k] else "fp64_fma",
                          # the solve reads the band twice: 16 (k+1) n bytes against the measured HBM copy rate
@@ -350,8 +357,8 @@ def run_ours(args, rank: int, world: int, dev: int):
                 "d2h_bytes_per_step": sum(8 * n + 4 for k in ks)},
         "roofline": {"bound": "alu", "achieved": round(achieved_tflops, 4), "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": round(achieved_tflops / FP64_PEAK_TFLOPS, 4),
-                     "traffic": (round(sum(TRAFFIC_N20000[k] for k in ks) * n / 20000 / len(ks))
-                                 if all(k in TRAFFIC_N20000 for k in ks) else None),
+                     "traffic": (round(sum(traffic_table(split_k[k])[k] for k in ks) * n / 20000 / len(ks))
+                                 if all(k in traffic_table(split_k[k]) for k in ks) else None),
                      "traffic_note": "DRAM bytes per factor launch, mean over the sweep's launches (ncu capture at "
                                      "n = 20000, scaled by n); per-k figures in per_k",
                      "kernel": "factor_kernel", "flops_per_launch": "n*k^2",
@@ -616,6 +623,22 @@ def cpu_baseline(n: int, ks: list[int], data=None, budget_s: float = 20.0) -> di
                       + ", ".join(samples)}
 
 
+def measure_peaks() -> dict:
+    """Delivered rates of the units behind the roofline denominators (bchol_probe_rate)."""
+    import ctypes
+    import paper_2305_04635_gb300 as bchol
+
+    h = bchol.Handle()
+    out = {}
+    for kind, name, iters in [(0, "fp64_dfma", 20000), (1, "fp64_dmma", 4000), (2, "fp32_ffma", 500000),
+                              (3, "bf16_tcgen05_mma", 500000)]:
+        r = ctypes.c_double()
+        rc = h._lib.bchol_probe_rate(h.ptr, kind, iters, ctypes.byref(r))
+        out[name + "_tflops"] = round(r.value, 2) if rc == 0 else f"error {rc}"
+    out["fp64_nominal_tflops"] = FP64_PEAK_TFLOPS
+    return out
+
+
 def barrier(world: int):
     if world > 1:
         torch.distributed.barrier()
@@ -648,6 +671,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-next", action="store_true", help="skip the batched, mixed and adjoint legs")
     ap.add_argument("--tile", type=int, default=0, help="tile size (0: automatic)")
+    ap.add_argument("--peaks", action="store_true", help="only measure the FP64/FP32/tensor unit rates and exit")
     ap.add_argument("--precision", default="split", choices=sorted(PRECISIONS),
                     help="trailing-update arithmetic: FP64 FMA, or FP64-accurate split products on the tensor cores")
     args = ap.parse_args()
@@ -678,6 +702,14 @@ def main():
         print(json.dumps(out))
         return
 
+    if args.peaks:
+        torch.cuda.set_device(local)
+        clocks = ClockSampler(local)
+        clocks.start()
+        peaks = measure_peaks()
+        peaks["clocks"] = clocks.stop()
+        print(json.dumps(peaks))
+        return
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
     out, data = run_ours(args, rank, world, local)

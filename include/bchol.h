@@ -345,6 +345,19 @@ bchol_status_t bchol_check_pivot_rcp(bchol_handle_t handle, const double* x, dou
 bchol_status_t bchol_check_split_product(bchol_handle_t handle, int m, int n, const double* A, int lda,
                                          const double* B, int ldb, double* C, int ldc);
 
+/* Throughput probe for the roofline denominators (not part of the paper's
+ * method): runs, on every SM, a loop of one instruction kind with independent
+ * accumulators and returns the delivered rate in TFLOP/s (synchronises):
+ *   kind 0  FP64 FMA (the unit of POTRF, TRSM and the FP64 updates)
+ *   kind 1  FP64 MMA, mma.sync m8n8k4 .f64 (shares the FP64 unit)
+ *   kind 2  FP32 FMA (the FP32_UPDATE mode's updates)
+ *   kind 3  bf16 tensor-core MMA, tcgen05.mma M = 128, N = 256, K = 16 with FP32
+ *           accumulators in tensor memory (the split updates' instruction)
+ * iters >= 1 sets the loop length (tens of milliseconds: 20000 for kinds 0-1,
+ * 500000 for 2-3).  Allocates a small scratch buffer with cudaMalloc.  Returns
+ * BCHOL_ERR_ARG on bad arguments, BCHOL_ERR_TIMEOUT if the tensor-core wait ran out. */
+bchol_status_t bchol_probe_rate(bchol_handle_t handle, int kind, int iters, double* tflops);
+
 /* Number of factor-kernel and solve-kernel launches made by the last call on
  * this handle (for launch accounting). */
 int bchol_last_launch_count(bchol_handle_t handle);

@@ -93,6 +93,7 @@ def load_library():
         "bchol_last_refinement": ([P, P, P, P], I),
         "bchol_check_pivot_rcp": ([P, P, P, I], I),
         "bchol_check_split_product": ([P, I, I, P, I, P, I, P, I], I),
+        "bchol_probe_rate": ([P, I, I, P], I),
         "bchol_adjoint_plan_task_count": ([I, I, I], ctypes.c_longlong),
         "bchol_adjoint_plan_task": ([I, I, I, ctypes.c_longlong, P, P, P, P], I),
         "bchol_version": ([], ctypes.c_char_p),

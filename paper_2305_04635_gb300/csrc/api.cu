@@ -318,6 +318,22 @@ bchol_status_t bchol_check_split_product(bchol_handle_t h, int m, int n, const d
   return BCHOL_OK;
 }
 
+bchol_status_t bchol_probe_rate(bchol_handle_t h, int kind, int iters, double* tflops) {
+  if (!h || kind < 0 || kind > 3 || iters < 1 || !tflops) return BCHOL_ERR_ARG;
+  char* ws = nullptr;
+  bchol_status_t rc = get_workspace(h, kStatusBytes, &ws);
+  if (rc != BCHOL_OK) return rc;
+  int* status = reinterpret_cast<int*>(ws);
+  h->last_status = status;
+  if (probe_rate(kind, iters, tflops, status, (uint64_t)h->wait_ms * 1000000ull, h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return BCHOL_ERR_CUDA;
+  }
+  int st = 0;
+  if (cudaMemcpy(&st, status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return BCHOL_ERR_CUDA;
+  return st != 0 ? BCHOL_ERR_TIMEOUT : BCHOL_OK;
+}
+
 int bchol_last_launch_count(bchol_handle_t h) { return h ? h->last_launches : 0; }
 
 const char* bchol_version(void) { return "bchol 0.1.0 (sm_103a)"; }

@@ -64,6 +64,10 @@ cudaError_t launch_solve_f32(int n, int k, int nrhs, const double* ab, long long
 
 int num_sms();
 
+// Throughput probes of the roofline denominators (probe.cu): TFLOP/s of kind
+// 0 DFMA, 1 DMMA, 2 FFMA, 3 tcgen05 bf16 MMA, over `iters` iterations per chain.
+cudaError_t probe_rate(int kind, int iters, double* tflops, int* status, uint64_t wait_ns, cudaStream_t stream);
+
 // The tensor-core split product alone (split.cu): C := C - A B^T, inner dimension 32.
 cudaError_t launch_split_check(int m, int n, const double* A, long long lda, const double* B, long long ldb,
                                double* C, long long ldc, int* status, int* abort_word, uint64_t wait_ns,
