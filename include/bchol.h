@@ -280,6 +280,17 @@ bchol_status_t bchol_last_refinement(bchol_handle_t handle, int* iters, double* 
 bchol_status_t bchol_set_wait_limit_ms(bchol_handle_t handle, int wait_limit_ms);
 bchol_status_t bchol_set_ctas_per_sm(bchol_handle_t handle, int ctas_per_sm);
 
+/* Algorithm of bchol_solve's FP64 sweeps (the result is the same to rounding):
+ *   0  automatic (the default): partitioned for 1 <= k <= 112 and n >= 2048, else cluster
+ *   1  cluster: the 32-row block chain on one thread-block cluster per group of
+ *      right-hand sides, far blocks on the cluster's worker CTAs
+ *   2  partitioned (for 1 <= k <= 112; other k use the cluster path): chunks of
+ *      256 rows solved independently, with k "spike" columns L_cc^{-1} L_{c,c-1}
+ *      per chunk, a sequential pass over the chunks' k boundary values, and a
+ *      second independent pass; n (k + nrhs) k multiply-adds per sweep
+ * Returns BCHOL_ERR_ARG for other values. */
+bchol_status_t bchol_set_solve_path(bchol_handle_t handle, int path);
+
 /* Test hook for the failure path.  While set to a tile (I, J) >= 0, the
  * factor kernel's waits on the ready flag of tile (I, J) (b x b tiles, block
  * row I, block column J, 0 <= I-J <= ceil(k/b)) get a target that is never

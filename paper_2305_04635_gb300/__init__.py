@@ -90,6 +90,7 @@ def load_library():
         "bchol_plan_task_count_ex": ([I, I, I, I], ctypes.c_longlong),
         "bchol_plan_task_ex": ([I, I, I, I, ctypes.c_longlong, P, P, P, P], I),
         "bchol_set_precision": ([P, I, I, ctypes.c_double], I),
+        "bchol_set_solve_path": ([P, I], I),
         "bchol_last_refinement": ([P, P, P, P], I),
         "bchol_check_pivot_rcp": ([P, P, P, I], I),
         "bchol_check_split_product": ([P, I, I, P, I, P, I, P, I], I),
@@ -149,6 +150,10 @@ class Handle:
         _check("bchol_last_refinement", self._lib.bchol_last_refinement(self._h, ctypes.byref(it), ctypes.byref(res),
                                                                         ctypes.byref(corr)))
         return it.value, res.value, corr.value
+
+    def set_solve_path(self, path: int) -> None:
+        """bchol_solve's FP64 algorithm: 0 automatic, 1 cluster chain, 2 partitioned (k <= 112)."""
+        _check("bchol_set_solve_path", self._lib.bchol_set_solve_path(self._h, path))
 
     def set_wait_limit_ms(self, ms: int) -> None:
         _check("bchol_set_wait_limit_ms", self._lib.bchol_set_wait_limit_ms(self._h, ms))

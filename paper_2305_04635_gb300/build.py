@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbchol.so")
-SOURCES = ["api.cu", "factor.cu", "solve.cu", "noalloc.cu", "batched.cu", "mixed.cu", "selinv.cu", "split.cu", "probe.cu"]
+SOURCES = ["api.cu", "factor.cu", "solve.cu", "noalloc.cu", "batched.cu", "mixed.cu", "selinv.cu", "split.cu", "probe.cu", "psolve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
 

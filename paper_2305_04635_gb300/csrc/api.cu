@@ -47,6 +47,7 @@ struct bchol_handle_s {
   const int* mixed_info = nullptr;
   int last_iters = 0;
   double last_resid = 0.0, last_corr = 0.0;
+  int solve_path = 0;  // 0 automatic, 1 cluster, 2 partitioned
 };
 
 using namespace bchol;
@@ -230,6 +231,12 @@ bchol_status_t bchol_set_precision(bchol_handle_t h, bchol_precision_t precision
   return BCHOL_OK;
 }
 
+bchol_status_t bchol_set_solve_path(bchol_handle_t h, int path) {
+  if (!h || path < 0 || path > 2) return BCHOL_ERR_ARG;
+  h->solve_path = path;
+  return BCHOL_OK;
+}
+
 bchol_status_t bchol_set_wait_limit_ms(bchol_handle_t h, int ms) {
   if (!h || ms < 1) return BCHOL_ERR_ARG;
   h->wait_ms = ms;
@@ -397,7 +404,8 @@ bchol_status_t bchol_solve(bchol_handle_t h, int n, int k, int nrhs, const doubl
   if (rc != BCHOL_OK) return rc;
   h->last_status = reinterpret_cast<int*>(ws);
   int launches = 0;
-  cudaError_t e = launch_solve(n, k, nrhs, ab, ldab, b, ldb, ws + kStatusBytes, &launches, h->stream);
+  cudaError_t e = launch_solve(n, k, nrhs, ab, ldab, b, ldb, ws + kStatusBytes, &launches, h->stream, h->solve_path,
+                               h->last_status, (uint64_t)h->wait_ms * 1000000ull);
   h->last_launches = launches;
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -438,7 +446,8 @@ bchol_status_t bchol_backward(bchol_handle_t h, int n, int k, const double* ab, 
     if (cudaMemcpyAsync(bbar, xbar, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
       return BCHOL_ERR_CUDA;
     int l2 = 0;
-    if (launch_solve(n, kk, 1, ab, ldab, bbar, n, ws + kStatusBytes, &l2, h->stream) != cudaSuccess) {
+    if (launch_solve(n, kk, 1, ab, ldab, bbar, n, ws + kStatusBytes, &l2, h->stream, 0, status,
+                     (uint64_t)h->wait_ms * 1000000ull) != cudaSuccess) {
       cudaGetLastError();
       return BCHOL_ERR_CUDA;
     }

@@ -56,8 +56,16 @@ cudaError_t launch_factor(const FactorPlan& plan, double* ab, long long ldab, in
 // Solve: block size and workspace of the inverted diagonal blocks.
 int solve_block(int k);
 size_t solve_workspace_bytes(int n, int k);
+// path: 0 automatic, 1 cluster, 2 partitioned; status (timeout record) and
+// wait_ns bound the partitioned solve's waits (without status it is not used).
 cudaError_t launch_solve(int n, int k, int nrhs, const double* ab, long long ldab, double* b, long long ldb,
-                         void* ws, int* launches, cudaStream_t stream);
+                         void* ws, int* launches, cudaStream_t stream, int path = 0, int* status = nullptr,
+                         uint64_t wait_ns = 2000000000ull);
+// The partitioned chunk solve for small k (psolve.cu).
+int psolve_max_k();
+size_t psolve_workspace_bytes(int n, int k);
+cudaError_t launch_psolve(int n, int k, int nrhs, const double* ab, long long ldab, double* b, long long ldb,
+                          void* ws, int* status, uint64_t wait_ns, int* launches, cudaStream_t stream);
 // The same sweeps with FP32 arithmetic (FP64 band and right-hand sides in memory).
 cudaError_t launch_solve_f32(int n, int k, int nrhs, const double* ab, long long ldab, double* b, long long ldb,
                              void* ws, int* launches, cudaStream_t stream);

@@ -19,6 +19,8 @@
 // barrier separates two rounds.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include "bchol_device.cuh"
 #include "bchol_internal.h"
 
@@ -38,9 +40,9 @@ constexpr size_t kBlk = (size_t)kSB * kSB;
 
 int solve_block(int) { return kSB; }
 
-size_t solve_workspace_bytes(int n, int) {
+size_t solve_workspace_bytes(int n, int k) {
   const size_t S = (size_t)((n + kSB - 1) / kSB);
-  return 3 * S * kBlk * sizeof(double);
+  return std::max(3 * S * kBlk * sizeof(double), psolve_workspace_bytes(n, k));
 }
 
 // Band entry L(gi, gj) (zero outside the band or the matrix).
@@ -425,8 +427,16 @@ static cudaError_t launch_solve_t(int n, int k, int nrhs, const double* ab, long
   return e;
 }
 
+// Path of the FP64 solve: the partitioned chunk solve (psolve.cu) for
+// 1 <= k <= psolve_max_k() and at least eight chunks, where the cluster chain's
+// per-block latency dominates; the cluster solve otherwise.  path: 0 automatic,
+// 1 cluster, 2 partitioned (where it applies).
 cudaError_t launch_solve(int n, int k, int nrhs, const double* ab, long long ldab, double* b, long long ldb, void* ws,
-                         int* launches, cudaStream_t stream) {
+                         int* launches, cudaStream_t stream, int path, int* status, uint64_t wait_ns) {
+  const int kk = (n > 0 && k > n - 1) ? n - 1 : k;
+  const bool part_ok = kk >= 1 && kk <= psolve_max_k() && status != nullptr;
+  const bool part = part_ok && (path == 2 || (path == 0 && n >= 8 * 256));
+  if (part) return launch_psolve(n, kk, nrhs, ab, ldab, b, ldb, ws, status, wait_ns, launches, stream);
   return launch_solve_t<double, kNRC>(n, k, nrhs, ab, ldab, b, ldb, ws, launches, stream);
 }
 

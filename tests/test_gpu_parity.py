@@ -223,3 +223,41 @@ def test_pivot_reciprocal_against_division():
     ulps = np.abs(y - 1.0 / x) / np.spacing(1.0 / x)
     print(f"pivot reciprocal: max |y x - 1| = {rel.max():.2e}, max error {ulps.max():.1f} ulp")
     assert rel.max() <= 4 * 2.0 ** -52 and ulps.max() <= 4
+
+
+@pytest.mark.parametrize("n,k,nrhs", [(300, 1, 1), (2048, 2, 3), (2049, 7, 1), (5000, 31, 9), (4000, 50, 17),
+                                      (2565, 50, 2), (3000, 63, 1), (2306, 64, 8), (200, 40, 3), (6000, 33, 1),
+                                      (3000, 100, 2), (2600, 112, 9), (4096, 112, 1)])
+def test_partitioned_solve_matches_oracle(n, k, nrhs):
+    """The partitioned solve (chunks of 256 rows, spike columns, boundary recurrence) against
+    the oracle's substitution on the oracle's factor, and against the cluster chain solve.
+    n = 2565, 2306 and 2600 leave a last chunk shorter than k (5, 2 and 40 rows)."""
+    L0, A, B = g.problem(n, k, seed=n + k, diag="log1e3", exact=False, nrhs=nrhs)
+    Lref, iref = oracle.pbtrf(A, k)
+    assert iref == 0
+    Xref = oracle.pbtrs(Lref, k, B)
+    xs = {}
+    for path in (2, 1):
+        h = bchol.Handle()
+        h.set_solve_path(path)
+        rc, info, L, X = run(A, k, B, handle=h, ldb_pad=1)
+        assert rc == 0 and info == 0
+        xs[path] = X
+    err = float(np.max(np.linalg.norm(xs[2] - Xref, axis=0) / np.linalg.norm(Xref, axis=0)))
+    d12 = float(np.max(np.linalg.norm(xs[2] - xs[1], axis=0) / np.linalg.norm(xs[1], axis=0)))
+    print(f"partitioned n={n} k={k} nrhs={nrhs}: rel err x {err:.2e}, vs cluster solve {d12:.2e}")
+    assert err <= TOL_X and d12 <= TOL_X
+
+
+@pytest.mark.parametrize("k", [50, 100])
+def test_partitioned_solve_at_full_size(k):
+    """n = 1e5, k = 50 and 100 (sweep matrices; automatic path = partitioned): x against the
+    oracle's substitution on L0 (the exact factor of the generated A)."""
+    n = 100000
+    L0, A, B = g.problem(n, k, seed=0, diag="log1e3", exact=True)
+    rc, info, L, X = run(A, k, B)
+    assert rc == 0 and info == 0
+    xref = oracle.pbtrs(L0, k, B[:, 0])
+    ex = float(np.linalg.norm(X[:, 0] - xref) / np.linalg.norm(xref))
+    print(f"partitioned n={n} k={k}: rel err x {ex:.2e}")
+    assert ex <= TOL_X
