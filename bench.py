@@ -382,10 +382,12 @@ def _colmajor(B: np.ndarray) -> torch.Tensor:
     return torch.from_numpy(np.ascontiguousarray(B.T)).cuda().T
 
 
-def next_batched(count: int = 512, reps: int = 3) -> dict:
+def next_batched(count: int = 512, reps: int = 3, precision: int = 3) -> dict:
     """512 independent systems, n log-uniform in [1e3, 5e4], k log-uniform in [50, 400], 4 RHS each:
     one graph-captured batched launch (autotuned tile and CTAs per SM) against a loop of the plain
-    per-matrix factor + solve on the same stream."""
+    per-matrix factor + solve on the same stream.  The batched launch runs in `precision` (split:
+    the trailing updates as split products on the tensor cores, in strips) and, for comparison,
+    with FP64 FMA updates."""
     import paper_2305_04635_gb300 as bchol
     from paper_2305_04635_gb300 import autotune
 
@@ -400,6 +402,7 @@ def next_batched(count: int = 512, reps: int = 3) -> dict:
     work = [p.clone() for p in pr]
     bw = [b.clone() for b in bpr]
     F = sum(flops_eq1(n, k) for n, k in zip(ns, ks))
+    nk2 = sum(flops_nk2(n, k) for n, k in zip(ns, ks))
 
     def restore():
         torch.cuda.synchronize()          # nothing may still be writing the work copies
@@ -431,58 +434,65 @@ def next_batched(count: int = 512, reps: int = 3) -> dict:
         raise RuntimeError("batched leg: a plain factorization failed")
     x_plain = [b.clone() for b in bw]
 
-    t1 = time.perf_counter()
-    tile, cps = autotune.tune_batch(pr, ks, bpr, handle=h)
-    tune_s = time.perf_counter() - t1
-    batch = bchol.Batch(work, ks, bw, tile=tile, ctas_per_sm=cps)
-    restore()
-    with torch.cuda.stream(stream):
-        batch.run(h)                      # workspace set-up outside the capture
-    torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph, stream=stream):
-        batch.run(h)
-    times = []
-    for _ in range(reps + 1):
+    def leg(prec):
+        t1 = time.perf_counter()
+        tile, cps = autotune.tune_batch(pr, ks, bpr, handle=h, precision=prec)
+        tune_s = time.perf_counter() - t1
+        batch = bchol.Batch(work, ks, bw, tile=tile, ctas_per_sm=cps, precision=prec)
         restore()
-        e0, e1 = _ev()
-        e0.record(stream)
         with torch.cuda.stream(stream):
-            graph.replay()
-        e1.record(stream)
+            batch.run(h)                  # workspace set-up outside the capture
         torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
-    batched_ms = statistics.median(times[1:])
-    if batch.info.cpu().tolist() != [0] * count:
-        raise RuntimeError("batched leg: a batched factorization failed")
-    diff = max(float(torch.linalg.norm(a - c) / torch.linalg.norm(c)) for a, c in zip(bw, x_plain))
-    batch.close()
-    # the factorizations alone (a batch without right-hand sides), for the factor / solve split
-    fbatch = bchol.Batch(work, ks, None, tile=tile, ctas_per_sm=cps)
-    ftimes = []
-    for _ in range(reps + 1):
-        restore()
-        e0, e1 = _ev()
-        e0.record(stream)
-        with torch.cuda.stream(stream):
-            fbatch.run(h)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ftimes.append(e0.elapsed_time(e1))
-    factor_ms = statistics.median(ftimes[1:])
-    fbatch.close()
-    nk2 = sum(flops_nk2(n, k) for n, k in zip(ns, ks))
-    return {"workload": f"{count} systems, n log-uniform [1e3,5e4], k log-uniform [50,400], 4 RHS, "
-                        "L0 diag log-uniform [1,1e3]",
-            "flops_eq1": F, "plain_loop_ms": round(plain_ms, 3), "batched_ms": round(batched_ms, 3),
-            "speedup_vs_plain": round(plain_ms / batched_ms, 3),
-            "batched_gflops_eq1": round(F / batched_ms / 1e6, 2),
-            "batched_factor_ms": round(factor_ms, 3), "batched_solve_ms": round(batched_ms - factor_ms, 3),
-            "factor_frac_fp64_roofline": round(nk2 / (factor_ms * 1e-3) / (FP64_PEAK_TFLOPS * 1e12), 4),
-            "factorizations_per_s": round(count / batched_ms * 1e3, 2),
-            "plain_factorizations_per_s": round(count / plain_ms * 1e3, 2),
-            "tile": tile, "ctas_per_sm": cps, "cuda_graph": True,
-            "max_rel_diff_x_vs_plain": diff, "gen_s": round(gen_s, 1), "tune_s": round(tune_s, 1)}
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            batch.run(h)
+        times = []
+        for _ in range(reps + 1):
+            restore()
+            e0, e1 = _ev()
+            e0.record(stream)
+            with torch.cuda.stream(stream):
+                graph.replay()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        batched_ms = statistics.median(times[1:])
+        if batch.info.cpu().tolist() != [0] * count:
+            raise RuntimeError("batched leg: a batched factorization failed")
+        diff = max(float(torch.linalg.norm(a - c) / torch.linalg.norm(c)) for a, c in zip(bw, x_plain))
+        batch.close()
+        # the factorizations alone (a batch without right-hand sides), for the factor / solve split
+        fbatch = bchol.Batch(work, ks, None, tile=tile, ctas_per_sm=cps, precision=prec)
+        ftimes = []
+        for _ in range(reps + 1):
+            restore()
+            e0, e1 = _ev()
+            e0.record(stream)
+            with torch.cuda.stream(stream):
+                fbatch.run(h)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ftimes.append(e0.elapsed_time(e1))
+        factor_ms = statistics.median(ftimes[1:])
+        fbatch.close()
+        return {"batched_ms": round(batched_ms, 3), "batched_factor_ms": round(factor_ms, 3),
+                "batched_solve_ms": round(batched_ms - factor_ms, 3),
+                "factor_frac_fp64_roofline": round(nk2 / (factor_ms * 1e-3) / (FP64_PEAK_TFLOPS * 1e12), 4),
+                "tile": tile, "ctas_per_sm": cps, "max_rel_diff_x_vs_plain": diff, "tune_s": round(tune_s, 1)}
+
+    main = leg(precision)
+    out = {"workload": f"{count} systems, n log-uniform [1e3,5e4], k log-uniform [50,400], 4 RHS, "
+                       "L0 diag log-uniform [1,1e3]",
+           "precision": "split" if precision == 3 else "fp64",
+           "flops_eq1": F, "plain_loop_ms": round(plain_ms, 3), "speedup_vs_plain": round(plain_ms / main["batched_ms"], 3),
+           "batched_gflops_eq1": round(F / main["batched_ms"] / 1e6, 2),
+           "factorizations_per_s": round(count / main["batched_ms"] * 1e3, 2),
+           "plain_factorizations_per_s": round(count / plain_ms * 1e3, 2), "cuda_graph": True,
+           "gen_s": round(gen_s, 1)}
+    out.update(main)
+    if precision != 0:
+        out["fp64_updates"] = leg(0)
+    return out
 
 
 def next_mixed(n: int = 200000, k: int = 1000, nrhs: int = 16, tol: float = 1e-10, reps: int = 2) -> dict:
@@ -714,7 +724,8 @@ def main():
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
     out, data = run_ours(args, rank, world, local)
     if not args.no_next:
-        out["next"] = {"batched": next_batched(), "mixed": next_mixed(), "adjoint": next_adjoint()}
+        out["next"] = {"batched": next_batched(precision=PRECISIONS[args.precision]), "mixed": next_mixed(),
+                       "adjoint": next_adjoint()}
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args.n, args.ks, budget_s=args.cpu_budget)

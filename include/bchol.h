@@ -232,6 +232,28 @@ bchol_status_t bchol_batch_plan(bchol_batch_t batch, int count, const int* n, co
                                 int tile, int ctas_per_sm);
 bchol_status_t bchol_batch_run(bchol_handle_t handle, bchol_batch_t batch);
 
+/* bchol_batch_set_precision -- the precision of the batch's next plan:
+ * BCHOL_FP64 (default) or BCHOL_FP64_SPLIT, which, with tiles of 16 or 32,
+ * runs every system's trailing updates as split products on the tensor cores
+ * in strips of 128 / b tiles (same accuracy contract as for bchol_factor;
+ * with tiles of 64 it plans the FP64 updates).  Takes effect at the next
+ * bchol_batch_plan.  BCHOL_ERR_UNSUPPORTED for BCHOL_FP32_UPDATE and
+ * BCHOL_TF32_UPDATE, BCHOL_ERR_ARG for an unknown mode.
+ * bchol_factor_batched plans with the handle's precision (FP64 when the
+ * handle's mode is BCHOL_FP32_UPDATE). */
+bchol_status_t bchol_batch_set_precision(bchol_batch_t batch, int precision);
+
+/* Schedule query of one system of a batch (host only): the batched kernel
+ * walks each system's tasks in the ticket order of bchol_plan_task with tile
+ * 64 (no diagonal chain), claiming whichever system's next task is ready.
+ * With BCHOL_FP64_SPLIT and tile 16 or 32 the updates of each block column
+ * are strips, type 3 = STRIP(I, J, s) of the tiles I .. min(I+H-1, s+m),
+ * H = 128/tile, each at the place of its first tile.  Count: -1 on bad
+ * arguments (n >= 1, k >= 0, tile 16/32/64, precision FP64 or FP64_SPLIT). */
+long long bchol_batch_plan_task_count(int n, int k, int tile, int precision);
+bchol_status_t bchol_batch_plan_task(int n, int k, int tile, int precision, long long ticket, int* type, int* s,
+                                     int* I, int* J);
+
 /* bchol_factor_batched -- plan + run in one call with the handle's own batch
  * object and its tile / CTA settings (arguments as for bchol_batch_plan). */
 bchol_status_t bchol_factor_batched(bchol_handle_t handle, int count, const int* n, const int* k, double* const* ab,

@@ -84,6 +84,9 @@ def load_library():
         "bchol_batch_destroy": ([P], I),
         "bchol_batch_plan": ([P, I, P, P, P, P, P, P, P, P, I, I], I),
         "bchol_batch_run": ([P, P], I),
+        "bchol_batch_set_precision": ([P, I], I),
+        "bchol_batch_plan_task_count": ([I, I, I, I], ctypes.c_longlong),
+        "bchol_batch_plan_task": ([I, I, I, I, ctypes.c_longlong, P, P, P, P], I),
         "bchol_factor_batched": ([P, I, P, P, P, P, P, P, P, P], I),
         "bchol_plan_task_count": ([I, I, I], ctypes.c_longlong),
         "bchol_plan_task": ([I, I, I, ctypes.c_longlong, P, P, P, P], I),
@@ -301,6 +304,21 @@ def plan_tasks(n: int, k: int, tile: int, precision: int = FP64) -> list[tuple[i
     return out
 
 
+def batch_plan_tasks(n: int, k: int, tile: int, precision: int = FP64) -> list[tuple[int, int, int, int]]:
+    """One system's task list in the batched kernel's ticket order (see bchol_batch_plan_task)."""
+    lib = load_library()
+    total = lib.bchol_batch_plan_task_count(n, k, tile, precision)
+    if total < 0:
+        raise ValueError("bad arguments")
+    out = []
+    t, s, I, J = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    for ticket in range(total):
+        _check("bchol_batch_plan_task", lib.bchol_batch_plan_task(n, k, tile, precision, ticket, ctypes.byref(t),
+                                                                  ctypes.byref(s), ctypes.byref(I), ctypes.byref(J)))
+        out.append((t.value, s.value, I.value, J.value))
+    return out
+
+
 def adjoint_plan_tasks(n: int, k: int, tile: int) -> list[tuple[int, int, int, int]]:
     """The selected inversion's task order as (type, J, I, g) (see bchol_adjoint_plan_task)."""
     lib = load_library()
@@ -325,7 +343,7 @@ class Batch:
     The plan keeps the tensors' addresses: run() may be captured in a CUDA graph.
     """
 
-    def __init__(self, bands, ks, rhs=None, tile: int = 0, ctas_per_sm: int = 0):
+    def __init__(self, bands, ks, rhs=None, tile: int = 0, ctas_per_sm: int = 0, precision: int = FP64):
         lib = load_library()
         self._lib = lib
         count = len(bands)
@@ -354,6 +372,7 @@ class Batch:
         self._keep = (list(bands), None if rhs is None else list(rhs), ns, kk, lds, ptrs, nr, bp, ldb)
         self._b = ctypes.c_void_p()
         _check("bchol_batch_create", lib.bchol_batch_create(ctypes.byref(self._b)))
+        _check("bchol_batch_set_precision", lib.bchol_batch_set_precision(self._b, precision))
         _check("bchol_batch_plan", lib.bchol_batch_plan(
             self._b, count, ns, kk, ptrs, lds, ctypes.c_void_p(self.info.data_ptr()),
             nr if rhs is not None else None, bp if rhs is not None else None, ldb if rhs is not None else None,

@@ -22,12 +22,12 @@ CANDIDATES = ((16, 1), (16, 2), (32, 1), (32, 2))
 _cache: dict[str, tuple[int, int]] = {}
 
 
-def signature(ns, ks) -> str:
-    """Batch class: count and the quartiles of n and k (log2-rounded)."""
+def signature(ns, ks, precision: int = 0) -> str:
+    """Batch class: count, the quantiles of n and k (log2-rounded) and the precision mode."""
     ns = np.asarray(ns, float)
     ks = np.asarray(ks, float)
     q = lambda v: [int(round(np.log2(max(1.0, x)) * 2)) for x in np.quantile(v, [0.1, 0.5, 0.9])]
-    return f"c{len(ns)}-n{q(ns)}-k{q(ks)}"
+    return f"c{len(ns)}-n{q(ns)}-k{q(ks)}" + (f"-p{precision}" if precision else "")
 
 
 def _load_file(path):
@@ -39,10 +39,10 @@ def _load_file(path):
 
 
 def tune_batch(bands, ks, rhs=None, candidates=CANDIDATES, reps: int = 1, cache_path: str | None = None,
-               handle: Handle | None = None) -> tuple[int, int]:
-    """Return (tile, ctas_per_sm) for this batch.  The inputs are not modified."""
+               handle: Handle | None = None, precision: int = 0) -> tuple[int, int]:
+    """Return (tile, ctas_per_sm) for this batch in the given precision mode.  The inputs are not modified."""
     ns = [int(b.shape[1]) for b in bands]
-    sig = signature(ns, ks)
+    sig = signature(ns, ks, precision)
     if cache_path:
         _cache.update(_load_file(cache_path))
     if sig in _cache:
@@ -52,7 +52,7 @@ def tune_batch(bands, ks, rhs=None, candidates=CANDIDATES, reps: int = 1, cache_
     rs = None if rhs is None else [None if r is None else r.clone() for r in rhs]
     best, best_ms = None, float("inf")
     for tile, cps in candidates:
-        batch = Batch(scratch, ks, rs, tile=tile, ctas_per_sm=cps)
+        batch = Batch(scratch, ks, rs, tile=tile, ctas_per_sm=cps, precision=precision)
         times = []
         for rep in range(reps + 1):
             for s, b in zip(scratch, bands):

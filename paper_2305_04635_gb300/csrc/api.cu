@@ -512,8 +512,9 @@ bchol_status_t bchol_factor_batched(bchol_handle_t h, int count, const int* n, c
     bchol_status_t rc = bchol_batch_create(&h->batch);
     if (rc != BCHOL_OK) return rc;
   }
-  bchol_status_t rc =
-      bchol_batch_plan(h->batch, count, n, k, ab, ldab, info_dev, nrhs, b, ldb, h->tile, h->ctas_per_sm);
+  bchol_status_t rc = bchol_batch_set_precision(h->batch, split_mode(h->precision) ? BCHOL_FP64_SPLIT : BCHOL_FP64);
+  if (rc != BCHOL_OK) return rc;
+  rc = bchol_batch_plan(h->batch, count, n, k, ab, ldab, info_dev, nrhs, b, ldb, h->tile, h->ctas_per_sm);
   if (rc != BCHOL_OK) return rc;
   return bchol_batch_run(h, h->batch);
 }

@@ -12,6 +12,10 @@
 // the launch cannot deadlock; a CTA that finds no ready task for longer than
 // the wait limit records a timeout and stops.  While one matrix's step chain
 // is busy, the CTAs work on the others, which hides the latency of the chain.
+// With the split updates (BCHOL_FP64_SPLIT, tiles of 16 or 32) each matrix's
+// trailing updates are strips of 128 / b tiles (decode_st_task), run as split
+// products on the tensor cores (strip_task.cuh); every CTA then holds 256
+// (tiles of 32) or 128 (tiles of 16) tensor-memory columns for its lifetime.
 //
 // Solve: one CTA per matrix, largest first, forward then back substitution
 // in blocks of 32 rows (band products of the far blocks spread over the
@@ -20,7 +24,8 @@
 #include <vector>
 
 #include "../../include/bchol.h"
-#include "factor_tasks.cuh"
+#include "bchol_internal.h"
+#include "strip_task.cuh"
 
 namespace bchol {
 
@@ -35,7 +40,7 @@ struct BatchMat {
   double* b;
   long long ldb;
   int nrhs;
-  int pad;
+  int H;                // strip height of the updates (1: one tile per update task)
 };
 
 struct BatchArgs {
@@ -53,6 +58,14 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
   unsigned long long v;
   asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
+}
+
+__device__ __forceinline__ void decode_mat_task(const FactorArgs& a, long long t, int& type, int& s, int& I, int& J) {
+  const Schedule sc{a.S, a.p, a.Sreg, a.Treg, a.H};
+  if (a.H > 1)
+    decode_st_task(sc, t, type, s, I, J);
+  else
+    decode_task(sc, t, type, s, I, J);
 }
 
 __device__ __forceinline__ FactorArgs matrix_args(const BatchArgs& g, int m) {
@@ -73,12 +86,21 @@ __device__ __forceinline__ FactorArgs matrix_args(const BatchArgs& g, int m) {
   a.info = M.info;
   a.wait_ns = g.wait_ns;
   a.stall = -1;
-  a.H = 1;
+  a.H = M.H;
   return a;
 }
 
 // Are the inputs of task (type, s, I, J) final?  The same targets as the waits in the tasks.
 __device__ __forceinline__ bool task_ready(const FactorArgs& a, int type, int s, int I, int J) {
+  if (type == kStrip) {  // STRIP(I, J, s): every tile's panel tile and previous update, and L_Js
+    const int h = strip_rows(a.H, s, min(a.p, a.S - 1 - s), I);
+    for (int t = 0; t < h; ++t) {
+      const int Ii = I + t, s0 = first_step(a, Ii);
+      if (ld_acquire(&a.flags[fidx(a, Ii, s)]) < s - s0 + 1 || ld_acquire(&a.flags[fidx(a, Ii, J)]) < s - s0)
+        return false;
+    }
+    return (J >= I && J < I + h) || ld_acquire(&a.flags[fidx(a, J, s)]) >= s - first_step(a, J) + 1;
+  }
   if (type == kPotrf) return ld_acquire(&a.flags[fidx(a, s, s)]) >= s - first_step(a, s);
   if (type == kTrsm)
     return ld_acquire(&a.flags[fidx(a, s, s)]) >= s - first_step(a, s) + 1 &&
@@ -88,12 +110,16 @@ __device__ __forceinline__ bool task_ready(const FactorArgs& a, int type, int s,
          ld_acquire(&a.flags[fidx(a, I, J)]) >= s - first_step(a, I);
 }
 
-template <int B>
+template <int B, bool TC>
 __global__ void __launch_bounds__(kThreads, 2) factor_batched_kernel(BatchArgs g) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   Smem<B>& sm = *reinterpret_cast<Smem<B>*>(smem_raw);
   __shared__ int s_m, s_go, s_flag;
   __shared__ long long s_t;
+  __shared__ unsigned long long s_mbar;
+  __shared__ uint32_t s_tmem;
+  split::Ctx cx{};
+  if constexpr (TC) cx = split::ctx_begin<B>(&s_mbar, &s_tmem);
   const int tid = threadIdx.x, lane = tid & 31;
   int m0 = blockIdx.x % g.count;   // where this CTA's search starts
   uint64_t idle_since = 0;
@@ -117,7 +143,7 @@ __global__ void __launch_bounds__(kThreads, 2) factor_batched_kernel(BatchArgs g
               if (atomicCAS(&c->retired, 0, 1) == 0) atomicAdd(g.retired, 1);
             } else {
               int type, s, I, J;
-              decode_task(Schedule{a.S, a.p, a.Sreg, a.Treg}, (long long)t, type, s, I, J);
+              decode_mat_task(a, (long long)t, type, s, I, J);
               ready = task_ready(a, type, s, I, J);
             }
           }
@@ -173,7 +199,15 @@ __global__ void __launch_bounds__(kThreads, 2) factor_batched_kernel(BatchArgs g
     }
     const FactorArgs a = matrix_args(g, s_m);
     int type, s, I, J;
-    decode_task(Schedule{a.S, a.p, a.Sreg, a.Treg}, s_t, type, s, I, J);
+    decode_mat_task(a, s_t, type, s, I, J);
+    if constexpr (TC) {
+      if (type == kStrip) {
+        // a product that did not complete leaves this CTA's barrier phase unknown: stop
+        if (!task_strip<B>(a, I, J, s, *reinterpret_cast<split::Smem<B>*>(smem_raw), cx, &s_flag)) break;
+        __syncthreads();
+        continue;
+      }
+    }
     if (type == kPotrf)
       task_potrf<B>(a, s, sm, &s_flag);
     else if (type == kTrsm)
@@ -182,6 +216,7 @@ __global__ void __launch_bounds__(kThreads, 2) factor_batched_kernel(BatchArgs g
       task_upd<B>(a, I, J, s, sm, &s_flag);
     __syncthreads();
   }
+  if constexpr (TC) split::ctx_end<B>(cx);
 }
 
 // ------------------------------------------------------------------ solve
@@ -303,10 +338,46 @@ __global__ void __launch_bounds__(256) solve_batched_kernel(const BatchMat* mats
 // ------------------------------------------------------------------ host side
 using namespace bchol;
 
+// Tickets of one system's strip order (decode_st_task).
+static unsigned long long st_total(const FactorPlan& P) {
+  const Schedule sc{P.S, P.p, P.Sreg, st_treg(P.p, P.H), P.H};
+  unsigned long long total = 1 + (unsigned long long)sched_m(sc, 0);
+  total += (unsigned long long)sc.Sreg * (unsigned long long)sc.Treg;
+  for (int s = (int)sc.Sreg; s < sc.S; ++s) total += (unsigned long long)st_block_size(sc, s);
+  return total;
+}
+
+static bool batch_query_args(int n, int k, int tile, int precision) {
+  return n >= 1 && k >= 0 && (tile == 16 || tile == 32 || tile == 64) &&
+         (precision == BCHOL_FP64 || precision == BCHOL_FP64_SPLIT);
+}
+
+extern "C" long long bchol_batch_plan_task_count(int n, int k, int tile, int precision) {
+  if (!batch_query_args(n, k, tile, precision)) return -1;
+  const FactorPlan P = make_factor_plan(n, std::min(k, n - 1), tile, precision == BCHOL_FP64_SPLIT);
+  return (long long)(P.H > 1 ? st_total(P) : P.total);
+}
+
+extern "C" bchol_status_t bchol_batch_plan_task(int n, int k, int tile, int precision, long long ticket, int* type,
+                                                int* s, int* I, int* J) {
+  if (!batch_query_args(n, k, tile, precision) || !type || !s || !I || !J) return BCHOL_ERR_ARG;
+  const FactorPlan P = make_factor_plan(n, std::min(k, n - 1), tile, precision == BCHOL_FP64_SPLIT);
+  const unsigned long long total = P.H > 1 ? st_total(P) : P.total;
+  if (ticket < 0 || (unsigned long long)ticket >= total) return BCHOL_ERR_ARG;
+  const Schedule sc{P.S, P.p, P.Sreg, P.H > 1 ? st_treg(P.p, P.H) : P.Treg, P.H};
+  if (P.H > 1)
+    decode_st_task(sc, ticket, *type, *s, *I, *J);
+  else
+    decode_task(sc, ticket, *type, *s, *I, *J);
+  return BCHOL_OK;
+}
+
 struct bchol_batch_s {
   int count = 0;
   int b = 32;
   int ctas_per_sm = 1;
+  int precision = BCHOL_FP64;   // BCHOL_FP64_SPLIT: updates as split products (tiles of 16 and 32)
+  bool split = false;           // the planned batch runs the split updates
   bool any_rhs = false;
   int* info_dev = nullptr;
   size_t bytes = 0;
@@ -327,6 +398,14 @@ extern "C" bchol_status_t bchol_batch_destroy(bchol_batch_t batch) {
   return BCHOL_OK;
 }
 
+extern "C" bchol_status_t bchol_batch_set_precision(bchol_batch_t batch, int precision) {
+  if (!batch) return BCHOL_ERR_ARG;
+  if (precision == BCHOL_FP32_UPDATE || precision == BCHOL_TF32_UPDATE) return BCHOL_ERR_UNSUPPORTED;
+  if (precision != BCHOL_FP64 && precision != BCHOL_FP64_SPLIT) return BCHOL_ERR_ARG;
+  batch->precision = precision;
+  return BCHOL_OK;
+}
+
 extern "C" bchol_status_t bchol_batch_plan(bchol_batch_t batch, int count, const int* n, const int* k, double* const* ab,
                                            const int* ldab, int* info_dev, const int* nrhs, double* const* b,
                                            const int* ldb, int tile, int ctas_per_sm) {
@@ -340,13 +419,14 @@ extern "C" bchol_status_t bchol_batch_plan(bchol_batch_t batch, int count, const
     kmax = std::max(kmax, std::min(k[m], n[m] - 1));
   }
   const int bt = tile ? tile : (kmax <= 256 ? 16 : 32);
+  const bool split = batch->precision == BCHOL_FP64_SPLIT && (bt == 16 || bt == 32);
   std::vector<BatchMat> mats(count);
   std::vector<double> work(count);
   size_t flag_total = 0;
   bool any_rhs = false;
   for (int m = 0; m < count; ++m) {
     const int kk = std::min(k[m], n[m] - 1);
-    const FactorPlan P = make_factor_plan(n[m], kk, bt);
+    const FactorPlan P = make_factor_plan(n[m], kk, bt, split);
     BatchMat& M = mats[m];
     M.ab = ab[m];
     M.ldab = ldab[m];
@@ -357,12 +437,16 @@ extern "C" bchol_status_t bchol_batch_plan(bchol_batch_t batch, int count, const
     M.Sreg = P.Sreg;
     M.Treg = P.Treg;
     M.total = P.total;
+    M.H = P.H;
+    if (P.H > 1) {  // the ticket-only order with strips (decode_st_task)
+      M.Treg = st_treg(P.p, P.H);
+      M.total = st_total(P);
+    }
     M.flag_off = (long long)flag_total;
     M.info = info_dev + m;
     M.nrhs = nrhs ? nrhs[m] : 0;
     M.b = M.nrhs ? b[m] : nullptr;
     M.ldb = M.nrhs ? ldb[m] : 1;
-    M.pad = 0;
     flag_total += P.flag_count;
     any_rhs = any_rhs || M.nrhs > 0;
     work[m] = (double)n[m] * (kk + 1.0) * (kk + 4.0);
@@ -407,23 +491,32 @@ extern "C" bchol_status_t bchol_batch_plan(bchol_batch_t batch, int count, const
     return BCHOL_ERR_CUDA;
   batch->count = count;
   batch->b = bt;
+  batch->split = split;
   batch->ctas_per_sm = ctas_per_sm ? ctas_per_sm : (kmax < 1536 ? 1 : 2);
   batch->any_rhs = any_rhs;
   batch->info_dev = info_dev;
   return BCHOL_OK;
 }
 
-template <int B>
+template <int B, bool TC = false>
 static cudaError_t launch_batched_factor(const BatchArgs& g, int ctas_per_sm, cudaStream_t st) {
-  const size_t smem = sizeof(Smem<B>);
-  cudaError_t e = cudaFuncSetAttribute(factor_batched_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = factor_batched_kernel<B, TC>;
+  size_t smem = sizeof(Smem<B>);
+  if constexpr (TC) smem = std::max(smem, sizeof(split::Smem<B>));
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, factor_batched_kernel<B>, kThreads, smem);
+  if constexpr (TC) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    e = tc_ctas_per_sm(reinterpret_cast<const void*>(kern), smem, split::tmem_cols<B>(), kThreads, &per_sm);
+  } else {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+  }
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
-  factor_batched_kernel<B><<<per_sm * num_sms(), kThreads, smem, st>>>(g);
+  kern<<<per_sm * num_sms(), kThreads, smem, st>>>(g);
   return cudaGetLastError();
 }
 
@@ -447,7 +540,10 @@ int batch_run(bchol_batch_s* batch, int* status, uint64_t wait_ns, cudaStream_t 
   g.status = status;
   g.wait_ns = wait_ns;
   cudaError_t e;
-  switch (batch->b) {
+  if (batch->split)
+    e = batch->b == 16 ? launch_batched_factor<16, true>(g, batch->ctas_per_sm, st)
+                       : launch_batched_factor<32, true>(g, batch->ctas_per_sm, st);
+  else switch (batch->b) {
     case 16: e = launch_batched_factor<16>(g, batch->ctas_per_sm, st); break;
     case 32: e = launch_batched_factor<32>(g, batch->ctas_per_sm, st); break;
     default: e = launch_batched_factor<64>(g, batch->ctas_per_sm, st); break;

@@ -47,6 +47,10 @@ long long plan_task_count(const FactorPlan& P);
 // Device workspace needed by one factorization (control block + flags).
 size_t factor_workspace_bytes(const FactorPlan& plan);
 
+// CTAs per SM of a kernel that allocates tmem_cols tensor-memory columns per
+// CTA, from its registers, shared memory (dyn_smem dynamic bytes) and threads.
+cudaError_t tc_ctas_per_sm(const void* func, size_t dyn_smem, int tmem_cols, int threads, int* per_sm);
+
 // Launch the persistent factor kernel.  `ws` holds factor_workspace_bytes()
 // bytes; `status` is a device int that outlives the call (timeout record).
 cudaError_t launch_pivot_rcp(const double* x, double* y, int n, cudaStream_t stream);

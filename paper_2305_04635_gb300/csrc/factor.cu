@@ -201,6 +201,28 @@ FactorPlan make_factor_plan(int n, int k, int b, bool split) {
 
 size_t factor_workspace_bytes(const FactorPlan& P) { return 256 + P.flag_count * sizeof(int); }
 
+// CTAs per SM of a kernel that allocates tensor memory.  The occupancy query
+// answers 1 for any such kernel, whatever it allocates; the SM runs as many
+// CTAs as its registers, shared memory and threads allow, and tcgen05.alloc
+// waits for columns, so the count comes from those resources and from the
+// SM's 512 tensor-memory columns.
+cudaError_t tc_ctas_per_sm(const void* func, size_t dyn_smem, int tmem_cols, int threads, int* per_sm) {
+  cudaFuncAttributes fa;
+  int dev = 0, smem_sm = 0, regs_sm = 0, reserved = 0;
+  cudaError_t e = cudaFuncGetAttributes(&fa, func);
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  if (e != cudaSuccess) return e;
+  const int regs_cta = (fa.numRegs + 7) / 8 * 8 * threads;
+  const int smem_cta = (int)(dyn_smem + fa.sharedSizeBytes) + reserved;
+  int fit = std::min(regs_sm / std::max(regs_cta, 1), smem_sm / std::max(smem_cta, 1));
+  fit = std::min({fit, 2048 / threads, 512 / std::max(tmem_cols, 1)});
+  *per_sm = std::max(1, fit);
+  return cudaSuccess;
+}
+
 template <int B, bool F32, int MODE, bool TC = false>
 static cudaError_t launch_b(const FactorArgs& a, int ctas_per_sm, cudaStream_t stream) {
   size_t smem = sizeof(Smem<B>);
@@ -222,24 +244,14 @@ static cudaError_t launch_b(const FactorArgs& a, int ctas_per_sm, cudaStream_t s
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
-  // The occupancy query answers 1 for any kernel that allocates tensor memory,
-  // whatever it allocates; the SM runs as many CTAs as its registers, shared
-  // memory and threads allow, and tcgen05.alloc waits for columns.  So the
-  // split kernels size their grid from those resources and from the tensor
-  // memory: each ticket CTA holds 256 (tiles of 32) or 128 (tiles of 16) of the
-  // SM's 512 columns.
+  // The split kernels size their grid from the SM's resources (tc_ctas_per_sm):
+  // each ticket CTA holds 256 (tiles of 32) or 128 (tiles of 16) of the SM's
+  // 512 tensor-memory columns.
   if constexpr (TC) {
-    cudaFuncAttributes fa;
-    int dev = 0, smem_sm = 0, regs_sm = 0, reserved = 0;
-    if (cudaFuncGetAttributes(&fa, factor_kernel<B, F32, MODE, TC>) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess)
-      return cudaErrorInvalidConfiguration;
-    const int regs_cta = (fa.numRegs + 7) / 8 * 8 * kThreads;
-    const int smem_cta = (int)(smem + fa.sharedSizeBytes) + reserved;
-    int fit = std::min(regs_sm / std::max(regs_cta, 1), smem_sm / std::max(smem_cta, 1));
-    fit = std::min({fit, 2048 / kThreads, (int)(512 / split::tmem_cols<B>())});
+    int fit = 0;
+    e = tc_ctas_per_sm(reinterpret_cast<const void*>(factor_kernel<B, F32, MODE, TC>), smem, split::tmem_cols<B>(),
+                       kThreads, &fit);
+    if (e != cudaSuccess) return e;
     per_sm = std::max(1, ctas_per_sm > 0 ? std::min(fit, ctas_per_sm) : fit);
   }
   long long grid = (long long)per_sm * num_sms();

@@ -327,4 +327,84 @@ __host__ __device__ inline void decode_hp_ticket(const Schedule& a, long long t,
   I = J = -1;
 }
 
+// ----------------------------------------------------------------------------
+// The ticket-only order (decode_task) with the updates in strips of H tiles,
+// for launches without a diagonal chain (the batched kernel): panel(0), then
+// for s = 0, 1, ...
+//     near(s)    STRIP(s+1+r, s+1, s), r = 0, H, 2H, ... < m_s
+//     panel(s+1) POTRF(s+1), TRSM(s+2+r, s+1), r < m_{s+1}
+//     far(s)     column J = s+2..s+m_s: STRIP(J+r, J, s), r = 0, H, ... <= s+m_s-J
+// A strip takes the place of its first tile in decode_task's order and its
+// tiles are consecutive there, so every dependency of that order still holds.
+// Regular blocks hold strips_of(p) + 1 + p + strips_upto(p-1) tickets.
+__host__ __device__ inline long long st_treg(int p, int H) {
+  return p >= 1 ? strips_of(p, H) + 1 + p + strips_upto(p - 1, H) : 1;
+}
+
+__host__ __device__ inline long long st_block_size(const Schedule& a, int s) {
+  const long long ms = sched_m(a, s);
+  const long long nxt = (s + 1 < a.S) ? 1 + sched_m(a, s + 1) : 0;
+  return strips_of(ms, a.H) + nxt + strips_upto(ms - 1, a.H);
+}
+
+__host__ __device__ inline void decode_st_task(const Schedule& a, long long t, int& type, int& s, int& I, int& J) {
+  const int m0 = sched_m(a, 0), H = a.H, sh = strip_shift(H);
+  if (t < 1 + m0) {  // panel(0)
+    s = J = 0;
+    type = t == 0 ? kPotrf : kTrsm;
+    I = (int)t;
+    return;
+  }
+  t -= 1 + m0;
+  if (t < a.Sreg * a.Treg) {
+    s = (int)(t / a.Treg);
+    t -= (long long)s * a.Treg;
+  } else {
+    t -= a.Sreg * a.Treg;
+    s = (int)a.Sreg;
+    while (s < a.S) {
+      const long long size = st_block_size(a, s);
+      if (t < size) break;
+      t -= size;
+      ++s;
+    }
+    if (s >= a.S) {
+      type = -1;  // past the last ticket
+      I = J = -1;
+      return;
+    }
+  }
+  const int ms = sched_m(a, s);
+  const long long nnear = strips_of(ms, H);
+  if (t < nnear) {  // near(s)
+    type = kStrip;
+    J = s + 1;
+    I = J + ((int)t << sh);
+    return;
+  }
+  t -= nnear;
+  if (s + 1 < a.S) {  // panel(s+1)
+    const int ms1 = sched_m(a, s + 1);
+    if (t < 1 + ms1) {
+      s = s + 1;
+      J = s;
+      type = t == 0 ? kPotrf : kTrsm;
+      I = s + (int)t;
+      return;
+    }
+    t -= 1 + ms1;
+  }
+  type = kStrip;  // far(s)
+  for (J = s + 2; J <= s + ms; ++J) {
+    const long long cnt = strips_of(s + ms - J + 1, H);
+    if (t < cnt) {
+      I = J + ((int)t << sh);
+      return;
+    }
+    t -= cnt;
+  }
+  type = -1;
+  I = J = -1;
+}
+
 }  // namespace bchol

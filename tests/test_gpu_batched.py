@@ -38,10 +38,17 @@ CASES = [(1, 0, 0, 1), (2, 1, 1, 2), (10, 3, 0, 0), (100, 31, 0, 1), (129, 64, 2
          (2000, 70, 0, 4), (4000, 300, 0, 1), (33, 32, 0, 9), (640, 100, 0, 4)]
 
 
-@pytest.mark.parametrize("tile,cps", [(0, 0), (16, 2), (32, 1), (32, 2)])
-def test_batched_matches_oracle(tile, cps):
+SPLIT = bchol.FP64_SPLIT
+
+
+@pytest.mark.parametrize("tile,cps,precision", [(0, 0, 0), (16, 2, 0), (32, 1, 0), (32, 2, 0), (0, 0, SPLIT),
+                                                (16, 1, SPLIT), (16, 2, SPLIT), (32, 1, SPLIT), (32, 2, SPLIT),
+                                                (64, 1, SPLIT)])
+def test_batched_matches_oracle(tile, cps, precision):
+    """Every system's L and x against the oracle; with the split mode (tiles of 16 and 32) the
+    trailing updates run as split products on the tensor cores, in strips."""
     probs, bands, rhs = _make(CASES)
-    batch = bchol.Batch(bands, [p[1] for p in probs], rhs, tile=tile, ctas_per_sm=cps)
+    batch = bchol.Batch(bands, [p[1] for p in probs], rhs, tile=tile, ctas_per_sm=cps, precision=precision)
     h = bchol.Handle()
     info = batch.run(h)
     rc, infos = bchol.get_info(info, handle=h)
@@ -57,17 +64,19 @@ def test_batched_matches_oracle(tile, cps):
             X = r.T.contiguous().cpu().numpy().T
             Xref = oracle.pbtrs(Lref, k, B)
             worst_x = max(worst_x, np.linalg.norm(X - Xref) / np.linalg.norm(Xref))
-    print(f"tile={tile} ctas/sm={cps}: worst rel err L {worst_L:.2e}, worst rel err x {worst_x:.2e}")
+    print(f"tile={tile} ctas/sm={cps} precision={precision}: worst rel err L {worst_L:.2e}, "
+          f"worst rel err x {worst_x:.2e}")
     assert worst_L <= TOL and worst_x <= TOL
 
 
-def test_batched_non_spd_member_is_isolated():
+@pytest.mark.parametrize("precision", [0, SPLIT])
+def test_batched_non_spd_member_is_isolated(precision):
     cases = [(1000, 40, 0, 1), (800, 60, 0, 1), (1200, 20, 0, 1)]
     probs, bands, rhs = _make(cases, seed=3)
     bad = g.dd_band(800, 60, seed=9)
     bad[0, 333] = -1.0e4
     bands[1] = bchol.band_from_numpy(bad)
-    batch = bchol.Batch(bands, [c[1] for c in cases], rhs)
+    batch = bchol.Batch(bands, [c[1] for c in cases], rhs, tile=32, precision=precision)
     h = bchol.Handle()
     rc, infos = bchol.get_info(batch.run(h), handle=h)
     assert rc == 1 and infos == [0, 334, 0]
@@ -79,13 +88,14 @@ def test_batched_non_spd_member_is_isolated():
         assert np.linalg.norm(X - Xref) / np.linalg.norm(Xref) <= TOL
 
 
-def test_batched_graph_capture_replays():
+@pytest.mark.parametrize("precision", [0, SPLIT])
+def test_batched_graph_capture_replays(precision):
     probs, bands, rhs = _make(CASES[5:12], seed=5)
     pristine = [b.clone() for b in bands]
     rhs0 = [None if r is None else r.clone() for r in rhs]
     stream = torch.cuda.Stream()
     h = bchol.Handle(stream=stream)
-    batch = bchol.Batch(bands, [p[1] for p in probs], rhs)
+    batch = bchol.Batch(bands, [p[1] for p in probs], rhs, tile=32, precision=precision)
     with torch.cuda.stream(stream):
         batch.run(h)                      # first run outside capture (workspace set-up)
     torch.cuda.synchronize()
@@ -147,3 +157,42 @@ def test_factor_batched_entry_point_and_autotuner(tmp_path):
         L = _band_cpu(ab)[: k + 1]
         valid = ~g.unused_mask(k + 1, k, n)
         assert np.linalg.norm((L - Lref)[valid]) / np.linalg.norm(Lref[valid]) <= TOL
+
+
+def test_batch_precision_arguments():
+    probs, bands, rhs = _make(CASES[3:5], seed=11)
+    for bad, code in ((bchol.FP32_UPDATE, 5), (bchol.TF32_UPDATE, 5), (7, -1)):
+        with pytest.raises(bchol.BcholError) as e:
+            bchol.Batch(bands, [p[1] for p in probs], rhs, precision=bad)
+        assert e.value.code == code
+
+
+def test_factor_batched_uses_the_handle_precision():
+    """bchol_factor_batched plans with the handle's split mode; the result matches the oracle."""
+    import ctypes
+    probs, bands, rhs = _make(CASES[6:13], seed=13)
+    ks = [p[1] for p in probs]
+    h = bchol.Handle(tile=32)
+    h.set_precision(SPLIT)
+    lib = bchol.load_library()
+    cnt = len(bands)
+    A = ctypes.c_int * cnt
+    Pp = ctypes.c_void_p * cnt
+    info = torch.zeros(cnt, dtype=torch.int32, device="cuda")
+    h._sync_stream()
+    rc = lib.bchol_factor_batched(h.ptr, cnt, A(*[b.shape[1] for b in bands]), A(*ks),
+                                  Pp(*[b.data_ptr() for b in bands]), A(*[b.stride(1) for b in bands]),
+                                  ctypes.c_void_p(info.data_ptr()), A(*[0 if r is None else r.shape[1] for r in rhs]),
+                                  Pp(*[None if r is None else r.data_ptr() for r in rhs]),
+                                  A(*[b.shape[1] for b in bands]))
+    assert rc == 0
+    rc, infos = bchol.get_info(info, handle=h)
+    assert rc == 0 and infos == [0] * cnt
+    for (n, k, A0, B), ab, r in zip(probs, bands, rhs):
+        Lref, _ = oracle.pbtrf(A0, k)
+        L = _band_cpu(ab)[: k + 1]
+        valid = ~g.unused_mask(k + 1, k, n)
+        assert np.linalg.norm((L - Lref)[valid]) / np.linalg.norm(Lref[valid]) <= TOL
+        if B is not None:
+            X = r.T.contiguous().cpu().numpy().T
+            assert np.linalg.norm(X - oracle.pbtrs(Lref, k, B)) / np.linalg.norm(oracle.pbtrs(Lref, k, B)) <= TOL

@@ -214,3 +214,43 @@ def test_split_launch_cannot_deadlock(n, k, b, workers):
                 ai[r] += 1
                 progress = True
         assert progress, f"stalled with {len(done)} of {total} tile tasks done"
+
+
+@pytest.mark.parametrize("b", [16, 32, 64])
+@pytest.mark.parametrize("n,k", [(1, 0), (100, 31), (100, 32), (3000, 130), (640, 200), (2000, 400), (700, 300),
+                                 (64, 63), (33, 32), (5000, 50), (200, 17), (500, 0), (40, 39), (1000, 65)])
+def test_batched_strip_order_covers_every_update_once_in_order(n, k, b):
+    """The batched kernel's per-system order (the ticket-only order, no diagonal chain): with the
+    split mode and tiles of 16 or 32 the updates of each block column run as strips of up to
+    128 / b tiles; expanded into tiles, every task of Algorithm 1 appears once and after every
+    task it reads, and the FP64 order is the tile-64 order of bchol_plan_task."""
+    H = 128 // b if b <= 32 else 1
+    got = bchol.batch_plan_tasks(n, k, b, precision=SPLIT)
+    want, S, p = expected_tasks(n, k, b)
+    if b <= 32 and p >= 2:
+        assert any(t[0] == 3 and len(_expand(t, S, p, H)) > 1 for t in got)
+    flat = [u for t in got for u in _expand(t, S, p, H)]
+    assert len(flat) == len(set(flat)) == len(want)
+    assert set(flat) == want
+    pos = {}
+    for i, t in enumerate(got):
+        for u in _expand(t, S, p, H):
+            pos[u] = i
+    for i, t in enumerate(got):
+        own = _expand(t, S, p, H)
+        for u in own:
+            for d in _deps(u, p):
+                if d not in own:
+                    assert pos[d] < i, (d, t)
+    fp64 = bchol.batch_plan_tasks(n, k, b)
+    assert all(t[0] != 3 for t in fp64) and set(fp64) == want
+    if b == 64:
+        assert fp64 == bchol.plan_tasks(n, k, 64)
+
+
+def test_batched_strip_order_rejects_bad_arguments():
+    lib = bchol.load_library()
+    assert lib.bchol_batch_plan_task_count(0, 0, 32, SPLIT) == -1
+    assert lib.bchol_batch_plan_task_count(100, 10, 48, SPLIT) == -1
+    assert lib.bchol_batch_plan_task_count(100, 10, 32, 1) == -1        # FP32_UPDATE has no batched form
+    assert lib.bchol_batch_plan_task_count(100, 10, 32, SPLIT) > 0
