@@ -18,12 +18,14 @@
 // (tiles of 32) or 128 (tiles of 16) tensor-memory columns for its lifetime.
 //
 // Solve: one CTA per matrix, largest first, forward then back substitution
-// in blocks of 32 rows (band products of the far blocks spread over the
-// CTA's warps, the 32 x 32 triangular solves on one warp with shuffles).
+// in blocks of 32 rows (batched_solve.cuh: the chain on four warps, one per
+// SM sub-partition, the far terms and the next block's tiles one block ahead
+// on the other four).
 #include <algorithm>
 #include <vector>
 
 #include "../../include/bchol.h"
+#include "batched_solve.cuh"
 #include "bchol_internal.h"
 #include "strip_task.cuh"
 
@@ -220,115 +222,39 @@ __global__ void __launch_bounds__(kThreads, 2) factor_batched_kernel(BatchArgs g
 }
 
 // ------------------------------------------------------------------ solve
-constexpr int kBS = 32;     // rows per block
-constexpr int kBR = 8;      // right-hand sides per pass
-
-__device__ __forceinline__ double lb(const BatchMat& M, int gi, int gj) {
-  const int d = gi - gj;
-  return (gi < M.n && gj >= 0 && d >= 0 && d <= M.k) ? __ldg(M.ab + d + (long long)gj * M.ldab) : 0.0;
-}
-
-// One warp: solve the 32 x 32 lower (fwd) or upper (L^T, bwd) triangle of diagonal block I
-// for v[r] (lane = row), r < nr.  Rows past n stay zero.
-template <bool fwd>
-__device__ __forceinline__ void tri_solve_warp(const BatchMat& M, int I, double (&v)[kBR], int nr, int lane) {
-  const int gi = I * kBS + lane;
-  const bool live = gi < M.n;
-  double col[kBS];   // fwd: L(i, j) for j (row i of the tile); bwd: L(j, i) for j (column i)
-#pragma unroll
-  for (int j = 0; j < kBS; ++j) col[j] = fwd ? lb(M, gi, I * kBS + j) : lb(M, I * kBS + j, gi);
-  const double rinv = live ? 1.0 / lb(M, gi, gi) : 0.0;
-#pragma unroll
-  for (int jj = 0; jj < kBS; ++jj) {
-    const int j = fwd ? jj : kBS - 1 - jj;
-#pragma unroll
-    for (int r = 0; r < kBR; ++r) {
-      if (r < nr) {
-        double x = (lane == j) ? v[r] * rinv : 0.0;
-        x = __shfl_sync(0xffffffffu, x, j);
-        if (lane == j) v[r] = x;
-        else if (fwd ? (lane > j) : (lane < j)) v[r] = fma(-col[j], x, v[r]);
-      }
-    }
-  }
-  if (!live) {
-#pragma unroll
-    for (int r = 0; r < kBR; ++r) v[r] = 0.0;
-  }
-}
-
-__global__ void __launch_bounds__(256) solve_batched_kernel(const BatchMat* mats, const int* order, int count,
-                                                            unsigned* queue) {
-  __shared__ double red[8][kBR][kBS];
+// One CTA per system with right-hand sides, largest first (batched_solve.cuh).
+__global__ void __launch_bounds__(bsolve::kThreads, 2) solve_batched_kernel(const BatchMat* mats, const int* order,
+                                                                           int count, unsigned* queue) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  bsolve::Smem& sm = *reinterpret_cast<bsolve::Smem*>(smem_raw);
   __shared__ int s_m;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int tid = threadIdx.x;
   while (true) {
     if (tid == 0) {
       const unsigned q = atomicAdd(queue, 1u);
       s_m = (q < (unsigned)count) ? order[q] : -1;
     }
     __syncthreads();
-    const int m = s_m;
+    const int mi = s_m;
     __syncthreads();
-    if (m < 0) break;
-    const BatchMat& M = mats[m];
-    if (M.nrhs <= 0 || M.n <= 0 || __ldcg(M.info) != 0) continue;
-    const int S = (M.n + kBS - 1) / kBS;
-    int P = (M.k + kBS - 1) / kBS;
-    if (P > S - 1) P = S - 1;
-    for (int c0 = 0; c0 < M.nrhs; c0 += kBR) {
-      const int nr = min(kBR, M.nrhs - c0);
-      double* bc = M.b + (long long)c0 * M.ldb;
-      for (int sweep = 0; sweep < 2; ++sweep) {
-        const bool fwd = (sweep == 0);
-        for (int step = 0; step < S; ++step) {
-          const int I = fwd ? step : S - 1 - step;
-          // far blocks: lane = row i of block I, warp w takes columns c = w, w+8, ...
-          double acc[kBR];
-#pragma unroll
-          for (int r = 0; r < kBR; ++r) acc[r] = 0.0;
-          const int jlo = fwd ? max(0, I - P) : I + 1;
-          const int jhi = fwd ? I - 1 : min(S - 1, I + P);
-          const int gi = I * kBS + lane;
-          for (int J = jlo; J <= jhi; ++J) {
-#pragma unroll
-            for (int q = 0; q < kBS / 8; ++q) {
-              const int gc = J * kBS + w + 8 * q;
-              if (gc < M.n) {
-                const double mv = fwd ? lb(M, gi, gc) : lb(M, gc, gi);
-#pragma unroll
-                for (int r = 0; r < kBR; ++r)
-                  if (r < nr) acc[r] = fma(mv, __ldcg(bc + gc + (long long)r * M.ldb), acc[r]);
-              }
-            }
-          }
-#pragma unroll
-          for (int r = 0; r < kBR; ++r)
-            if (r < nr) red[w][r][lane] = acc[r];
-          __syncthreads();
-          if (w == 0) {
-            double v[kBR];
-#pragma unroll
-            for (int r = 0; r < kBR; ++r) {
-              v[r] = 0.0;
-              if (r < nr) {
-                double s = 0.0;
-#pragma unroll
-                for (int ww = 0; ww < 8; ++ww) s += red[ww][r][lane];
-                v[r] = (gi < M.n ? __ldcg(bc + gi + (long long)r * M.ldb) : 0.0) - s;
-              }
-            }
-            if (fwd)
-              tri_solve_warp<true>(M, I, v, nr, lane);
-            else
-              tri_solve_warp<false>(M, I, v, nr, lane);
-#pragma unroll
-            for (int r = 0; r < kBR; ++r)
-              if (r < nr && gi < M.n) bc[gi + (long long)r * M.ldb] = v[r];
-          }
-          __syncthreads();
-        }
-      }
+    if (mi < 0) break;
+    const BatchMat& M = mats[mi];
+    const int nrhs = M.nrhs, n = M.n;
+    if (nrhs <= 0 || n <= 0 || __ldcg(M.info) != 0) continue;
+    bsolve::Sys sy;
+    sy.ab = M.ab;
+    sy.ldab = M.ldab;
+    sy.n = n;
+    sy.k = M.k;
+    sy.S = (n + bsolve::kB - 1) / bsolve::kB;
+    sy.P = min((M.k + bsolve::kB - 1) / bsolve::kB, sy.S - 1);
+    double* const b = M.b;
+    const long long ldb = M.ldb;
+    for (int c0 = 0; c0 < nrhs; c0 += bsolve::kR) {
+      const int nr = min(bsolve::kR, nrhs - c0);
+      double* bc = b + (long long)c0 * ldb;
+      bsolve::sweep<true>(sm, sy, bc, ldb, nr);
+      bsolve::sweep<false>(sm, sy, bc, ldb, nr);
     }
   }
 }
@@ -552,9 +478,20 @@ int batch_run(bchol_batch_s* batch, int* status, uint64_t wait_ns, cudaStream_t 
   *launches = 1;
   if (batch->any_rhs) {
     unsigned* queue = reinterpret_cast<unsigned*>(base + batch->cnt_off + 64);
-    const int grid = std::min(batch->count, 4 * num_sms());
-    solve_batched_kernel<<<grid, 256, 0, st>>>(g.mats, reinterpret_cast<const int*>(base + batch->order_off),
-                                               batch->count, queue);
+    const size_t smem = sizeof(bsolve::Smem);
+    if (cudaFuncSetAttribute(solve_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(solve_batched_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+      return BCHOL_ERR_CUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_batched_kernel, bsolve::kThreads, smem) !=
+            cudaSuccess ||
+        per_sm < 1)
+      return BCHOL_ERR_CUDA;
+    const int grid = std::min(batch->count, per_sm * num_sms());
+    solve_batched_kernel<<<grid, bsolve::kThreads, smem, st>>>(
+        g.mats, reinterpret_cast<const int*>(base + batch->order_off), batch->count, queue);
     if (cudaGetLastError() != cudaSuccess) return BCHOL_ERR_CUDA;
     *launches = 2;
   }
