@@ -43,6 +43,7 @@ struct BatchMat {
   long long ldb;
   int nrhs;
   int H;                // strip height of the updates (1: one tile per update task)
+  long long part_off;   // solve: offset (doubles) of this system's worker partial sums in the pool
 };
 
 struct BatchArgs {
@@ -222,23 +223,40 @@ __global__ void __launch_bounds__(kThreads, 2) factor_batched_kernel(BatchArgs g
 }
 
 // ------------------------------------------------------------------ solve
-// One CTA per system with right-hand sides, largest first (batched_solve.cuh).
-__global__ void __launch_bounds__(bsolve::kThreads, 2) solve_batched_kernel(const BatchMat* mats, const int* order,
-                                                                           int count, unsigned* queue) {
+// CTAs take roles from a queue, largest system first: role 0 of a system is
+// its leader (the chain and the near far terms), roles 1..W its workers (the
+// other far terms; batched_solve.cuh).  A system's roles are consecutive in
+// the queue and every CTA of the launch is resident, so a leader never waits
+// on a role that no CTA will take: the systems ahead of it in the queue have
+// all their roles running and finish.
+struct SolveArgs {
+  const BatchMat* mats;
+  const int* entries;   // (system << 4) | role
+  int nent;
+  unsigned* queue;
+  int* ctl;             // kCtlInts per system
+  double* part;
+  int* status;
+  uint64_t wait_ns;
+};
+
+__global__ void __launch_bounds__(bsolve::kThreads, 2) solve_batched_kernel(SolveArgs sa) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   bsolve::Smem& sm = *reinterpret_cast<bsolve::Smem*>(smem_raw);
-  __shared__ int s_m;
+  bsolve::WSmem& ws = *reinterpret_cast<bsolve::WSmem*>(smem_raw);
+  __shared__ int s_e;
   const int tid = threadIdx.x;
   while (true) {
     if (tid == 0) {
-      const unsigned q = atomicAdd(queue, 1u);
-      s_m = (q < (unsigned)count) ? order[q] : -1;
+      const unsigned q = atomicAdd(sa.queue, 1u);
+      s_e = (q < (unsigned)sa.nent) ? sa.entries[q] : -1;
     }
     __syncthreads();
-    const int mi = s_m;
+    const int e = s_e;
     __syncthreads();
-    if (mi < 0) break;
-    const BatchMat& M = mats[mi];
+    if (e < 0) break;
+    const int mi = e >> 4, role = e & 15;
+    const BatchMat& M = sa.mats[mi];
     const int nrhs = M.nrhs, n = M.n;
     if (nrhs <= 0 || n <= 0 || __ldcg(M.info) != 0) continue;
     bsolve::Sys sy;
@@ -248,14 +266,28 @@ __global__ void __launch_bounds__(bsolve::kThreads, 2) solve_batched_kernel(cons
     sy.k = M.k;
     sy.S = (n + bsolve::kB - 1) / bsolve::kB;
     sy.P = min((M.k + bsolve::kB - 1) / bsolve::kB, sy.S - 1);
+    bsolve::Group G;
+    G.W = bsolve::workers_for(sy.P);
+    G.span = bsolve::worker_span(sy.P, G.W);
+    G.ctl = sa.ctl + (size_t)mi * bsolve::kCtlInts;
+    G.part = sa.part + M.part_off;
+    G.status = sa.status;
+    G.wait_ns = sa.wait_ns;
     double* const b = M.b;
     const long long ldb = M.ldb;
-    for (int c0 = 0; c0 < nrhs; c0 += bsolve::kR) {
+    for (int c0 = 0, pass = 0; c0 < nrhs; c0 += bsolve::kR, ++pass) {
       const int nr = min(bsolve::kR, nrhs - c0);
       double* bc = b + (long long)c0 * ldb;
-      bsolve::sweep<true>(sm, sy, bc, ldb, nr);
-      bsolve::sweep<false>(sm, sy, bc, ldb, nr);
+      const long long base = 2LL * pass * sy.S;
+      if (role == 0) {
+        bsolve::sweep<true>(sm, sy, bc, ldb, nr, G, base);
+        bsolve::sweep<false>(sm, sy, bc, ldb, nr, G, base + sy.S);
+      } else if (!bsolve::worker_sweep_nr<true>(ws, sy, bc, ldb, nr, G, role, base) ||
+                 !bsolve::worker_sweep_nr<false>(ws, sy, bc, ldb, nr, G, role, base + sy.S)) {
+        break;
+      }
     }
+    __syncthreads();
   }
 }
 
@@ -307,8 +339,9 @@ struct bchol_batch_s {
   bool any_rhs = false;
   int* info_dev = nullptr;
   size_t bytes = 0;
-  void* dev = nullptr;          // descriptors | order | control | flags | counters
-  size_t ctl_off = 0, flags_off = 0, cnt_off = 0, order_off = 0, clear_bytes = 0;
+  void* dev = nullptr;          // descriptors | solve roles | control | flags | counters | solve control | partial sums
+  size_t ctl_off = 0, flags_off = 0, cnt_off = 0, order_off = 0, sctl_off = 0, part_off = 0, clear_bytes = 0;
+  int nent = 0;                 // solve roles
 };
 
 extern "C" bchol_status_t bchol_batch_create(bchol_batch_t* batch) {
@@ -383,15 +416,28 @@ extern "C" bchol_status_t bchol_batch_plan(bchol_batch_t batch, int count, const
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
   std::vector<BatchMat> sorted(count);
   for (int q = 0; q < count; ++q) sorted[q] = mats[order[q]];
-  std::vector<int> solve_order(count);
-  for (int q = 0; q < count; ++q) solve_order[q] = q;   // indices into the sorted descriptors
+  // solve roles: each system with right-hand sides, its leader then its workers
+  std::vector<int> roles;
+  long long part_total = 0;
+  for (int q = 0; q < count; ++q) {
+    BatchMat& M = sorted[q];
+    M.part_off = part_total;
+    if (M.nrhs <= 0) continue;
+    const int S = (M.n + bsolve::kB - 1) / bsolve::kB;
+    const int P = std::min((M.k + bsolve::kB - 1) / bsolve::kB, S - 1);
+    const int W = bsolve::workers_for(P);
+    for (int r = 0; r <= W; ++r) roles.push_back((q << 4) | r);
+    part_total += (long long)W * bsolve::kSlots * bsolve::kR * bsolve::kB;
+  }
   auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
   const size_t desc_b = up(sizeof(BatchMat) * count);
-  const size_t order_b = up(sizeof(int) * count);
+  const size_t order_b = up(sizeof(int) * std::max<size_t>(roles.size(), 1));
   const size_t ctl_b = up(sizeof(Control) * count);
   const size_t flags_b = up(sizeof(int) * flag_total);
   const size_t cnt_b = 256;
-  const size_t need = desc_b + order_b + ctl_b + flags_b + cnt_b;
+  const size_t sctl_b = up(sizeof(int) * bsolve::kCtlInts * count);
+  const size_t part_b = up(sizeof(double) * (size_t)part_total);
+  const size_t need = desc_b + order_b + ctl_b + flags_b + cnt_b + sctl_b + part_b;
   if (batch->bytes < need) {
     if (batch->dev) {
       cudaDeviceSynchronize();
@@ -410,10 +456,14 @@ extern "C" bchol_status_t bchol_batch_plan(bchol_batch_t batch, int count, const
   batch->ctl_off = desc_b + order_b;
   batch->flags_off = batch->ctl_off + ctl_b;
   batch->cnt_off = batch->flags_off + flags_b;
-  batch->clear_bytes = ctl_b + flags_b + cnt_b;   // control, flags and counters are contiguous
+  batch->sctl_off = batch->cnt_off + cnt_b;
+  batch->part_off = batch->sctl_off + sctl_b;
+  batch->clear_bytes = ctl_b + flags_b + cnt_b + sctl_b;   // control, flags, counters, solve control: contiguous
+  batch->nent = (int)roles.size();
   if (cudaMemcpy(base, sorted.data(), sizeof(BatchMat) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(base + batch->order_off, solve_order.data(), sizeof(int) * count, cudaMemcpyHostToDevice) !=
-          cudaSuccess)
+      (!roles.empty() &&
+       cudaMemcpy(base + batch->order_off, roles.data(), sizeof(int) * roles.size(), cudaMemcpyHostToDevice) !=
+           cudaSuccess))
     return BCHOL_ERR_CUDA;
   batch->count = count;
   batch->b = bt;
@@ -476,8 +526,16 @@ int batch_run(bchol_batch_s* batch, int* status, uint64_t wait_ns, cudaStream_t 
   }
   if (e != cudaSuccess) return BCHOL_ERR_CUDA;
   *launches = 1;
-  if (batch->any_rhs) {
-    unsigned* queue = reinterpret_cast<unsigned*>(base + batch->cnt_off + 64);
+  if (batch->any_rhs && batch->nent > 0) {
+    SolveArgs sa;
+    sa.mats = g.mats;
+    sa.entries = reinterpret_cast<const int*>(base + batch->order_off);
+    sa.nent = batch->nent;
+    sa.queue = reinterpret_cast<unsigned*>(base + batch->cnt_off + 64);
+    sa.ctl = reinterpret_cast<int*>(base + batch->sctl_off);
+    sa.part = reinterpret_cast<double*>(base + batch->part_off);
+    sa.status = status;
+    sa.wait_ns = wait_ns;
     const size_t smem = sizeof(bsolve::Smem);
     if (cudaFuncSetAttribute(solve_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess ||
@@ -489,9 +547,9 @@ int batch_run(bchol_batch_s* batch, int* status, uint64_t wait_ns, cudaStream_t 
             cudaSuccess ||
         per_sm < 1)
       return BCHOL_ERR_CUDA;
-    const int grid = std::min(batch->count, per_sm * num_sms());
-    solve_batched_kernel<<<grid, bsolve::kThreads, smem, st>>>(
-        g.mats, reinterpret_cast<const int*>(base + batch->order_off), batch->count, queue);
+    // every CTA resident at once (the groups' waits rely on it)
+    const int grid = std::min(batch->nent, per_sm * num_sms());
+    solve_batched_kernel<<<grid, bsolve::kThreads, smem, st>>>(sa);
     if (cudaGetLastError() != cudaSuccess) return BCHOL_ERR_CUDA;
     *launches = 2;
   }

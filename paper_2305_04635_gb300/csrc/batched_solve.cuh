@@ -43,6 +43,21 @@ constexpr int kXP = kB + 1;   // pitch of the published block (doubles)
 constexpr int kBarChain = 1;  // warps 0-3
 constexpr int kBarFar = 2;    // warps 4-7
 constexpr int kDepth = 4;     // far blocks in the asynchronous-copy ring (a power of two)
+// Worker CTAs (systems with P >= kMinPW): worker w = 1..W owns the far
+// distances 3 + (w-1) span .. + span - 1 of every target block.
+constexpr int kMinPW = 5;
+constexpr int kMaxW = 15;
+constexpr int kWD = 2;        // far distances per worker when the count allows
+constexpr int kSlots = 8;     // ring slots of a worker's partial sums (global memory)
+constexpr int kMaxD = 4;      // far blocks per worker pass over shared memory
+constexpr int kCtlInts = 64;  // per system: [0] blocks solved by the leader, [1] abort, [32 + w] targets done by worker w
+
+__host__ __device__ inline int workers_for(int P) {
+  if (P < kMinPW) return 0;
+  const int w = (P - 2 + kWD - 1) / kWD;
+  return w < kMaxW ? w : kMaxW;
+}
+__host__ __device__ inline int worker_span(int P, int W) { return W > 0 ? (P - 2 + W - 1) / W : 0; }
 
 struct Smem {
   double T[2][2][kB][kTP];   // [slot][0: diagonal tile, 1: near tile][row][col]
@@ -60,6 +75,39 @@ struct Sys {
   long long ldab;
   int n, k, S, P;
 };
+
+// A system's leader / worker group: control words, the workers' partial sums
+// (part[((w-1) kSlots + slot) kR kB + r kB + row]), the launch status word.
+struct Group {
+  int W, span;
+  int* ctl;
+  double* part;
+  int* status;
+  uint64_t wait_ns;
+};
+
+// Shared memory of a worker CTA (aliases Smem).
+struct WSmem {
+  double ys[kMaxD][kB][kR];   // solved values of the blocks of one pass (column, rhs)
+  double red[8][kR][kB];      // per-warp partial sums
+};
+
+// One thread: wait until *flag >= target.  False when the group is aborted or
+// the wait runs out (then the launch status records a timeout and the abort
+// word stops the group's other waits).
+__device__ __forceinline__ bool gwait(const Group& G, const int* flag, int target) {
+  if (ld_acquire(flag) >= target) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (true) {
+    if (ld_acquire(flag) >= target) return true;
+    if (ld_relaxed(&G.ctl[1]) != 0) return false;
+    if (globaltimer_ns() - t0 > G.wait_ns) {
+      atomicExch(G.status, kStatusTimeout);
+      atomicExch(&G.ctl[1], 1);
+      return false;
+    }
+  }
+}
 
 __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
@@ -92,7 +140,7 @@ __device__ __forceinline__ const double* laddr(const Sys& m, int gi, int gj) {
 // the band's latency overlaps the FMAs instead of preceding each block.
 template <bool FWD, int NR>
 __device__ __forceinline__ void far_step(Smem& sm, const Sys& m, const double* bc, long long ldb, int nr, int slot,
-                                         int It, int fw, int p) {
+                                         int It, int fw, int p, const Group& G, long long g, int tt) {
   const int ft = fw * 32 + p;
   const int g0 = It * kB, gp = g0 + p;
 #pragma unroll
@@ -111,8 +159,9 @@ __device__ __forceinline__ void far_step(Smem& sm, const Sys& m, const double* b
     if (r < nr && gp < m.n) cp_async8(d, bc + gp + (long long)r * ldb); else *d = 0.0;
   }
   cp_commit();
-  const int jlo = FWD ? max(0, It - m.P) : It + 2;
-  const int jhi = FWD ? It - 2 : min(m.S - 1, It + m.P);
+  const int dmax = G.W > 0 ? 2 : m.P;   // with workers this CTA keeps distance 2 only
+  const int jlo = FWD ? max(0, It - dmax) : It + 2;
+  const int jhi = FWD ? It - 2 : min(m.S - 1, It + dmax);
   const int ycol = ft >> 2, yr = ft & 3;   // the solved value this thread fetches for each block
   auto issue = [&](int J) {
     const int sl = (J - jlo) & (kDepth - 1);
@@ -158,11 +207,24 @@ __device__ __forceinline__ void far_step(Smem& sm, const Sys& m, const double* b
 #pragma unroll
   for (int r = 0; r < kR; ++r) sm.red[fw][r][p] = r < NR ? acc[r < NR ? r : 0] : 0.0;
   cp_wait<0>();
-  bar_sync(kBarFar, 128);   // tiles, b and partial sums of all four warps are in
+  if (G.W > 0 && fw == 0 && p == 0) {   // the workers' partial sums of this target (step tt, global index g)
+    for (int w = 1; w <= G.W; ++w) {
+      const int dlo = 3 + (w - 1) * G.span;
+      if (dlo <= m.P && dlo <= tt) gwait(G, &G.ctl[32 + w], (int)(g + 1));
+    }
+  }
+  bar_sync(kBarFar, 128);   // tiles, b, partial sums of all four warps and of the workers are in
   if (fw == 0) sm.rinv[slot][p] = pivot_rcp(sm.T[slot][0][p][p]);
   {
     const int r = fw;
-    sm.U[slot][r][p] = sm.bpre[r][p] - ((sm.red[0][r][p] + sm.red[1][r][p]) + (sm.red[2][r][p] + sm.red[3][r][p]));
+    double ext = 0.0;
+    for (int w = 1; w <= G.W; ++w) {
+      const int dlo = 3 + (w - 1) * G.span;
+      if (dlo <= m.P && dlo <= tt)
+        ext += __ldcg(G.part + ((size_t)((w - 1) * kSlots + (int)(g % kSlots)) * kR + r) * kB + p);
+    }
+    sm.U[slot][r][p] =
+        sm.bpre[r][p] - ((sm.red[0][r][p] + sm.red[1][r][p]) + (sm.red[2][r][p] + sm.red[3][r][p]) + ext);
   }
   bar_sync(kBarFar, 128);
 #pragma unroll
@@ -228,21 +290,24 @@ __device__ __forceinline__ void chain_step(Smem& sm, const Sys& m, double* bc, l
   }
 }
 
+// Leader: one sweep (steps base .. base + S - 1 in the group's global step count).
 template <bool FWD>
-__device__ __forceinline__ void sweep(Smem& sm, const Sys& m, double* bc, long long ldb, int nr) {
+__device__ __forceinline__ void sweep(Smem& sm, const Sys& m, double* bc, long long ldb, int nr, const Group& G,
+                                      long long base) {
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const bool chain = w < 4;
   const int fw = w - 4;
   const int I0 = FWD ? 0 : m.S - 1;
-  auto far = [&](int slot, int It) {   // the right-hand-side count as a template argument: no idle FMAs
+  auto far = [&](int slot, int It, int tt) {   // the right-hand-side count as a template argument: no idle FMAs
+    const long long g = base + tt;
     switch (nr) {
-      case 1: far_step<FWD, 1>(sm, m, bc, ldb, nr, slot, It, fw, lane); break;
-      case 2: far_step<FWD, 2>(sm, m, bc, ldb, nr, slot, It, fw, lane); break;
-      case 3: far_step<FWD, 3>(sm, m, bc, ldb, nr, slot, It, fw, lane); break;
-      default: far_step<FWD, 4>(sm, m, bc, ldb, nr, slot, It, fw, lane); break;
+      case 1: far_step<FWD, 1>(sm, m, bc, ldb, nr, slot, It, fw, lane, G, g, tt); break;
+      case 2: far_step<FWD, 2>(sm, m, bc, ldb, nr, slot, It, fw, lane, G, g, tt); break;
+      case 3: far_step<FWD, 3>(sm, m, bc, ldb, nr, slot, It, fw, lane, G, g, tt); break;
+      default: far_step<FWD, 4>(sm, m, bc, ldb, nr, slot, It, fw, lane, G, g, tt); break;
     }
   };
-  if (!chain) far(0, I0);   // the first block has no far terms
+  if (!chain) far(0, I0, 0);   // the first block has no far terms
   __syncthreads();
   double nacc = 0.0;
   for (int t = 0; t < m.S; ++t) {
@@ -250,9 +315,97 @@ __device__ __forceinline__ void sweep(Smem& sm, const Sys& m, double* bc, long l
     if (chain) {
       chain_step<FWD>(sm, m, bc, ldb, nr, t & 1, I, w, lane & 7, lane >> 3, nacc);
     } else if (t + 1 < m.S) {
-      far((t + 1) & 1, FWD ? I + 1 : I - 1);
+      far((t + 1) & 1, FWD ? I + 1 : I - 1, t + 1);
     }
     __syncthreads();
+    if (G.W > 0 && tid == 128) {   // publish block I (all of its stores precede the barrier)
+      __threadfence();
+      st_release(&G.ctl[0], (int)(base + t + 1));
+    }
+  }
+}
+
+// Worker w: for every target block of the sweep that has blocks at its far
+// distances, once the leader has solved them, the partial sum over those
+// blocks (lane = row, the 32 columns of a block over the 8 warps) into ring
+// slot g % kSlots, then its done count.  It never runs more than kSlots
+// targets ahead of the leader's reads.  Returns false when the group aborts.
+template <bool FWD, int NR>
+__device__ bool worker_sweep(WSmem& ws, const Sys& m, const double* bc, long long ldb, int nr, const Group& G, int w,
+                             long long base) {
+  const int dlo = 3 + (w - 1) * G.span, dhi = min(m.P, dlo + G.span - 1);
+  if (dlo > dhi) return true;
+  const int tid = threadIdx.x, w8 = tid >> 5, p = tid & 31;
+  __shared__ int s_ok;
+  for (int t = dlo; t < m.S; ++t) {
+    const int It = FWD ? t : m.S - 1 - t;
+    const long long g = base + t;
+    const int dtop = min(dhi, t);
+    if (tid == 0) s_ok = gwait(G, &G.ctl[0], (int)max(g - dlo + 1, g - kSlots));
+    __syncthreads();
+    if (!s_ok) return false;
+    double acc[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] = 0.0;
+    for (int d0 = dlo; d0 <= dtop; d0 += kMaxD) {
+      const int nd = min(kMaxD, dtop - d0 + 1);
+      for (int e = tid; e < nd * kB * kR; e += kThreads) {
+        const int dd = e / (kB * kR), col = (e / kR) % kB, r = e % kR;
+        const int J = FWD ? It - (d0 + dd) : It + (d0 + dd);
+        const int gq = J * kB + col;
+        ws.ys[dd][col][r] = (r < nr && gq < m.n) ? __ldcg(bc + gq + (long long)r * ldb) : 0.0;
+      }
+      double lv[kMaxD][kB / 8];
+#pragma unroll
+      for (int dd = 0; dd < kMaxD; ++dd) {
+        const int J = FWD ? It - (d0 + dd) : It + (d0 + dd);
+#pragma unroll
+        for (int u = 0; u < kB / 8; ++u) {
+          const int gq = J * kB + w8 + 8 * u;
+          const double* src = dd < nd ? (FWD ? laddr(m, It * kB + p, gq) : laddr(m, gq, It * kB + p)) : nullptr;
+          lv[dd][u] = src ? __ldg(src) : 0.0;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int dd = 0; dd < kMaxD; ++dd)
+        if (dd < nd) {
+#pragma unroll
+          for (int u = 0; u < kB / 8; ++u) {
+            const double* y = ws.ys[dd][w8 + 8 * u];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) acc[r] = fma(lv[dd][u], y[r], acc[r]);
+          }
+        }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < kR; ++r) ws.red[w8][r][p] = r < NR ? acc[r < NR ? r : 0] : 0.0;
+    __syncthreads();
+    if (tid < kR * kB) {
+      const int r = tid >> 5, row = tid & 31;
+      double v = 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v += ws.red[q][r][row];
+      G.part[((size_t)((w - 1) * kSlots + (int)(g % kSlots)) * kR + r) * kB + row] = v;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      st_release(&G.ctl[32 + w], (int)(g + 1));
+    }
+  }
+  return true;
+}
+
+template <bool FWD>
+__device__ bool worker_sweep_nr(WSmem& ws, const Sys& m, const double* bc, long long ldb, int nr, const Group& G,
+                                int w, long long base) {
+  switch (nr) {
+    case 1: return worker_sweep<FWD, 1>(ws, m, bc, ldb, nr, G, w, base);
+    case 2: return worker_sweep<FWD, 2>(ws, m, bc, ldb, nr, G, w, base);
+    case 3: return worker_sweep<FWD, 3>(ws, m, bc, ldb, nr, G, w, base);
+    default: return worker_sweep<FWD, 4>(ws, m, bc, ldb, nr, G, w, base);
   }
 }
 
