@@ -250,6 +250,17 @@ bchol_status_t bchol_batch_set_precision(bchol_batch_t batch, int precision);
  * are strips, type 3 = STRIP(I, J, s) of the tiles I .. min(I+H-1, s+m),
  * H = 128/tile, each at the place of its first tile.  Count: -1 on bad
  * arguments (n >= 1, k >= 0, tile 16/32/64, precision FP64 or FP64_SPLIT). */
+/* The batched solve's group for one system (host only): with P = ceil(k/32)
+ * blocks of 32 rows below each diagonal block (at most ceil(n/32) - 1), a
+ * leader CTA runs the substitution chain and the far terms at block distance
+ * 2, and `workers` extra CTAs (0 when P < 5) take the distances >= 3, worker
+ * w = 1..workers the distances 3 + (w-1) span .. min(P, 2 + w span).  Each
+ * worker passes its partial sums through a ring of `slots` slots.  ctas > 0:
+ * the CTAs the solve launch keeps resident; no group is planned larger than
+ * that (bchol_batch_plan uses the device's count).  BCHOL_ERR_ARG for n < 1,
+ * k < 0 or a null pointer. */
+bchol_status_t bchol_batch_solve_group(int n, int k, int ctas, int* workers, int* span, int* slots);
+
 long long bchol_batch_plan_task_count(int n, int k, int tile, int precision);
 bchol_status_t bchol_batch_plan_task(int n, int k, int tile, int precision, long long ticket, int* type, int* s,
                                      int* I, int* J);

@@ -85,6 +85,7 @@ def load_library():
         "bchol_batch_plan": ([P, I, P, P, P, P, P, P, P, P, I, I], I),
         "bchol_batch_run": ([P, P], I),
         "bchol_batch_set_precision": ([P, I], I),
+        "bchol_batch_solve_group": ([I, I, I, P, P, P], I),
         "bchol_batch_plan_task_count": ([I, I, I, I], ctypes.c_longlong),
         "bchol_batch_plan_task": ([I, I, I, I, ctypes.c_longlong, P, P, P, P], I),
         "bchol_factor_batched": ([P, I, P, P, P, P, P, P, P, P], I),
@@ -317,6 +318,16 @@ def batch_plan_tasks(n: int, k: int, tile: int, precision: int = FP64) -> list[t
                                                                   ctypes.byref(s), ctypes.byref(I), ctypes.byref(J)))
         out.append((t.value, s.value, I.value, J.value))
     return out
+
+
+def batch_solve_group(n: int, k: int, ctas: int = 0) -> tuple[int, int, int]:
+    """(workers, span, slots) of the batched solve's group for one system on a launch that keeps
+    `ctas` CTAs resident (0: no limit); see bchol_batch_solve_group."""
+    lib = load_library()
+    w, sp, sl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check("bchol_batch_solve_group", lib.bchol_batch_solve_group(n, k, ctas, ctypes.byref(w), ctypes.byref(sp),
+                                                                  ctypes.byref(sl)))
+    return w.value, sp.value, sl.value
 
 
 def adjoint_plan_tasks(n: int, k: int, tile: int) -> list[tuple[int, int, int, int]]:

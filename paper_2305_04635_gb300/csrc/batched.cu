@@ -44,6 +44,8 @@ struct BatchMat {
   int nrhs;
   int H;                // strip height of the updates (1: one tile per update task)
   long long part_off;   // solve: offset (doubles) of this system's worker partial sums in the pool
+  int W;                // solve: worker CTAs of this system (batched_solve.cuh)
+  int pad2;
 };
 
 struct BatchArgs {
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(bsolve::kThreads, 2) solve_batched_kernel(Solv
     sy.S = (n + bsolve::kB - 1) / bsolve::kB;
     sy.P = min((M.k + bsolve::kB - 1) / bsolve::kB, sy.S - 1);
     bsolve::Group G;
-    G.W = bsolve::workers_for(sy.P);
+    G.W = M.W;
     G.span = bsolve::worker_span(sy.P, G.W);
     G.ctl = sa.ctl + (size_t)mi * bsolve::kCtlInts;
     G.part = sa.part + M.part_off;
@@ -296,6 +298,20 @@ __global__ void __launch_bounds__(bsolve::kThreads, 2) solve_batched_kernel(Solv
 // ------------------------------------------------------------------ host side
 using namespace bchol;
 
+// Resident CTAs of the solve launch (its grid when it has that many roles).
+static cudaError_t solve_capacity(int* cap) {
+  const size_t smem = sizeof(bsolve::Smem);
+  cudaError_t e = cudaFuncSetAttribute(solve_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(solve_batched_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  int per_sm = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_batched_kernel, bsolve::kThreads, smem);
+  if (e != cudaSuccess) return e;
+  *cap = std::max(1, per_sm) * num_sms();
+  return cudaSuccess;
+}
+
 // Tickets of one system's strip order (decode_st_task).
 static unsigned long long st_total(const FactorPlan& P) {
   const Schedule sc{P.S, P.p, P.Sreg, st_treg(P.p, P.H), P.H};
@@ -308,6 +324,16 @@ static unsigned long long st_total(const FactorPlan& P) {
 static bool batch_query_args(int n, int k, int tile, int precision) {
   return n >= 1 && k >= 0 && (tile == 16 || tile == 32 || tile == 64) &&
          (precision == BCHOL_FP64 || precision == BCHOL_FP64_SPLIT);
+}
+
+extern "C" bchol_status_t bchol_batch_solve_group(int n, int k, int ctas, int* workers, int* span, int* slots) {
+  if (n < 1 || k < 0 || !workers || !span || !slots) return BCHOL_ERR_ARG;
+  const int S = (n + bsolve::kB - 1) / bsolve::kB;
+  const int P = std::min((std::min(k, n - 1) + bsolve::kB - 1) / bsolve::kB, S - 1);
+  *workers = bsolve::workers_for(P, ctas);
+  *span = bsolve::worker_span(P, *workers);
+  *slots = bsolve::kSlots;
+  return BCHOL_OK;
 }
 
 extern "C" long long bchol_batch_plan_task_count(int n, int k, int tile, int precision) {
@@ -416,16 +442,22 @@ extern "C" bchol_status_t bchol_batch_plan(bchol_batch_t batch, int count, const
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
   std::vector<BatchMat> sorted(count);
   for (int q = 0; q < count; ++q) sorted[q] = mats[order[q]];
-  // solve roles: each system with right-hand sides, its leader then its workers
+  // solve roles: each system with right-hand sides, its leader then its
+  // workers; no group larger than the CTAs the solve launch keeps resident
+  int cap = 0;
+  if (any_rhs && solve_capacity(&cap) != cudaSuccess) return BCHOL_ERR_CUDA;
   std::vector<int> roles;
   long long part_total = 0;
   for (int q = 0; q < count; ++q) {
     BatchMat& M = sorted[q];
     M.part_off = part_total;
+    M.W = 0;
+    M.pad2 = 0;
     if (M.nrhs <= 0) continue;
     const int S = (M.n + bsolve::kB - 1) / bsolve::kB;
     const int P = std::min((M.k + bsolve::kB - 1) / bsolve::kB, S - 1);
-    const int W = bsolve::workers_for(P);
+    const int W = bsolve::workers_for(P, cap);
+    M.W = W;
     for (int r = 0; r <= W; ++r) roles.push_back((q << 4) | r);
     part_total += (long long)W * bsolve::kSlots * bsolve::kR * bsolve::kB;
   }
@@ -537,18 +569,10 @@ int batch_run(bchol_batch_s* batch, int* status, uint64_t wait_ns, cudaStream_t 
     sa.status = status;
     sa.wait_ns = wait_ns;
     const size_t smem = sizeof(bsolve::Smem);
-    if (cudaFuncSetAttribute(solve_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(solve_batched_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
-      return BCHOL_ERR_CUDA;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_batched_kernel, bsolve::kThreads, smem) !=
-            cudaSuccess ||
-        per_sm < 1)
-      return BCHOL_ERR_CUDA;
-    // every CTA resident at once (the groups' waits rely on it)
-    const int grid = std::min(batch->nent, per_sm * num_sms());
+    int cap = 0;
+    if (solve_capacity(&cap) != cudaSuccess) return BCHOL_ERR_CUDA;
+    // every CTA resident at once, and no group larger than the grid (the plan's cap)
+    const int grid = std::min(batch->nent, cap);
     solve_batched_kernel<<<grid, bsolve::kThreads, smem, st>>>(sa);
     if (cudaGetLastError() != cudaSuccess) return BCHOL_ERR_CUDA;
     *launches = 2;

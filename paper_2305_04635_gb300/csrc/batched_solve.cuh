@@ -44,7 +44,8 @@ constexpr int kBarChain = 1;  // warps 0-3
 constexpr int kBarFar = 2;    // warps 4-7
 constexpr int kDepth = 4;     // far blocks in the asynchronous-copy ring (a power of two)
 // Worker CTAs (systems with P >= kMinPW): worker w = 1..W owns the far
-// distances 3 + (w-1) span .. + span - 1 of every target block.
+// distances 3 + (w-1) span .. + span - 1 of every target block.  The plan caps
+// W below the launch's resident CTAs, so that every group can be staffed.
 constexpr int kMinPW = 5;
 constexpr int kMaxW = 15;
 constexpr int kWD = 2;        // far distances per worker when the count allows
@@ -52,12 +53,19 @@ constexpr int kSlots = 8;     // ring slots of a worker's partial sums (global m
 constexpr int kMaxD = 4;      // far blocks per worker pass over shared memory
 constexpr int kCtlInts = 64;  // per system: [0] blocks solved by the leader, [1] abort, [32 + w] targets done by worker w
 
-__host__ __device__ inline int workers_for(int P) {
-  if (P < kMinPW) return 0;
-  const int w = (P - 2 + kWD - 1) / kWD;
-  return w < kMaxW ? w : kMaxW;
-}
 __host__ __device__ inline int worker_span(int P, int W) { return W > 0 ? (P - 2 + W - 1) / W : 0; }
+// Workers of a system with P far blocks on a launch of `cap` resident CTAs
+// (cap <= 0: no limit): kWD distances each, at most kMaxW and cap - 1, then
+// as few as cover the distances 3..P at the resulting span (none idle).
+__host__ __device__ inline int workers_for(int P, int cap = 0) {
+  if (P < kMinPW) return 0;
+  int w = (P - 2 + kWD - 1) / kWD;
+  if (w > kMaxW) w = kMaxW;
+  if (cap > 0 && w > cap - 1) w = cap - 1;
+  if (w <= 0) return 0;
+  const int span = worker_span(P, w);
+  return (P - 2 + span - 1) / span;
+}
 
 struct Smem {
   double T[2][2][kB][kTP];   // [slot][0: diagonal tile, 1: near tile][row][col]
