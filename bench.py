@@ -669,6 +669,45 @@ def job_rate(world: int, flops_per_rank: float, steps: int, wall: float) -> floa
     return world * flops_per_rank * steps / wall / 1e9
 
 
+def batched_case(count: int, n_scale: int, nrhs: int, precision: int, n: int = 0, k: int = 0,
+                 reps: int = 3) -> dict:
+    """A small batched case for profiling: the batch leg's shape draw (count systems, n divided by
+    n_scale) or, with n and k given, that one system; nrhs right-hand sides each (0: factor only);
+    tile 32, 2 CTAs/SM.  Runs the plan `reps` times and reports each run's CUDA-event time."""
+    import paper_2305_04635_gb300 as bchol
+
+    if n > 0:
+        ns, ks = [n], [k]
+    else:
+        ns, ks = bandgen.batch_shapes(count, seed=0)
+        ns = [max(1000, v // n_scale) for v in ns]
+    bands = [bchol.band_from_numpy(bandgen.band_product(bandgen.l0_band(nn, kk, 0, "log1e3", matrix_id=m), kk))
+             for m, (nn, kk) in enumerate(zip(ns, ks))]
+    rhs = [_colmajor(bandgen.rhs(nn, nrhs, 0, m)) for m, nn in enumerate(ns)] if nrhs > 0 else None
+    b0 = [b.clone() for b in bands]
+    r0 = None if rhs is None else [r.clone() for r in rhs]
+    batch = bchol.Batch(bands, ks, rhs, tile=32, ctas_per_sm=2, precision=precision)
+    h = bchol.Handle()
+    times = []
+    for _ in range(reps):
+        for b, c in zip(bands, b0):
+            b.copy_(c)
+        if rhs is not None:
+            for r, c in zip(rhs, r0):
+                r.copy_(c)
+        torch.cuda.synchronize()
+        e0, e1 = _ev()
+        e0.record()
+        batch.run(h)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(round(e0.elapsed_time(e1), 3))
+    if batch.info.cpu().tolist() != [0] * len(ns):
+        raise RuntimeError("batched case: a factorization failed")
+    batch.close()
+    return {"case": "batched", "systems": len(ns), "n_scale": n_scale, "nrhs": nrhs, "ms": times}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -684,6 +723,13 @@ def main():
     ap.add_argument("--peaks", action="store_true", help="only measure the FP64/FP32/tensor unit rates and exit")
     ap.add_argument("--precision", default="split", choices=sorted(PRECISIONS),
                     help="trailing-update arithmetic: FP64 FMA, or FP64-accurate split products on the tensor cores")
+    ap.add_argument("--case", default="", choices=["", "batched"],
+                    help="only run a small case for profiling and print its times (batched: --count systems of the "
+                         "batch leg's draw with n divided by --n-scale, or one system with --system n,k)")
+    ap.add_argument("--count", type=int, default=96)
+    ap.add_argument("--n-scale", type=int, default=4)
+    ap.add_argument("--nrhs", type=int, default=0)
+    ap.add_argument("--system", type=lambda s: [int(x) for x in s.split(",")], default=None)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -712,6 +758,11 @@ def main():
         print(json.dumps(out))
         return
 
+    if args.case == "batched":
+        torch.cuda.set_device(local)
+        n, k = args.system if args.system else (0, 0)
+        print(json.dumps(batched_case(args.count, args.n_scale, args.nrhs, PRECISIONS[args.precision], n, k)))
+        return
     if args.peaks:
         torch.cuda.set_device(local)
         clocks = ClockSampler(local)
