@@ -436,9 +436,14 @@ def next_batched(count: int = 512, reps: int = 3, precision: int = 3) -> dict:
 
     def leg(prec):
         t1 = time.perf_counter()
-        tile, cps = autotune.tune_batch(pr, ks, bpr, handle=h, precision=prec)
+        classes, member = None, None
+        if prec == 3:   # split: the update mode per (n, k) class as well
+            plan = autotune.tune_batch_classes(pr, ks, bpr, handle=h)
+            tile, cps, classes, member = plan["tile"], plan["ctas_per_sm"], plan["classes"], plan["member_precision"]
+        else:
+            tile, cps = autotune.tune_batch(pr, ks, bpr, handle=h, precision=prec)
         tune_s = time.perf_counter() - t1
-        batch = bchol.Batch(work, ks, bw, tile=tile, ctas_per_sm=cps, precision=prec)
+        batch = bchol.Batch(work, ks, bw, tile=tile, ctas_per_sm=cps, precision=prec, member_precision=member)
         restore()
         with torch.cuda.stream(stream):
             batch.run(h)                  # workspace set-up outside the capture
@@ -462,7 +467,7 @@ def next_batched(count: int = 512, reps: int = 3, precision: int = 3) -> dict:
         diff = max(float(torch.linalg.norm(a - c) / torch.linalg.norm(c)) for a, c in zip(bw, x_plain))
         batch.close()
         # the factorizations alone (a batch without right-hand sides), for the factor / solve split
-        fbatch = bchol.Batch(work, ks, None, tile=tile, ctas_per_sm=cps, precision=prec)
+        fbatch = bchol.Batch(work, ks, None, tile=tile, ctas_per_sm=cps, precision=prec, member_precision=member)
         ftimes = []
         for _ in range(reps + 1):
             restore()
@@ -478,7 +483,9 @@ def next_batched(count: int = 512, reps: int = 3, precision: int = 3) -> dict:
         return {"batched_ms": round(batched_ms, 3), "batched_factor_ms": round(factor_ms, 3),
                 "batched_solve_ms": round(batched_ms - factor_ms, 3),
                 "factor_frac_fp64_roofline": round(nk2 / (factor_ms * 1e-3) / (FP64_PEAK_TFLOPS * 1e12), 4),
-                "tile": tile, "ctas_per_sm": cps, "max_rel_diff_x_vs_plain": diff, "tune_s": round(tune_s, 1)}
+                "tile": tile, "ctas_per_sm": cps, "max_rel_diff_x_vs_plain": diff, "tune_s": round(tune_s, 1),
+                **({"class_modes": {c: ("split" if m == 3 else "fp64") for c, m in classes.items()}}
+                   if classes else {})}
 
     main = leg(precision)
     out = {"workload": f"{count} systems, n log-uniform [1e3,5e4], k log-uniform [50,400], 4 RHS, "

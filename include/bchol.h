@@ -218,7 +218,8 @@ bchol_status_t bchol_solve_mixed(bchol_handle_t handle, int n, int k, int nrhs, 
  *   info_dev         DEVICE array of count ints: per-system info (LAPACK convention)
  *   nrhs, b, ldb     optional (NULL = no solve): HOST arrays; b holds DEVICE pointers to
  *                    n x nrhs column-major blocks, overwritten by X = A^{-1} B
- *   tile             16, 32 or 64 (0 = automatic); ctas_per_sm 0 = automatic
+ *   tile             16, 32 or 64 (0 = automatic: 32); ctas_per_sm 0 = automatic (2, or fewer
+ *                    where the SM's resources allow fewer)
  * bchol_batch_plan synchronises (it copies the descriptors to the device).
  * bchol_batch_run only enqueues a memset and two kernels on the handle's
  * stream, so it can be captured in a CUDA graph and replayed; the pointed-to
@@ -242,6 +243,15 @@ bchol_status_t bchol_batch_run(bchol_handle_t handle, bchol_batch_t batch);
  * bchol_factor_batched plans with the handle's precision (FP64 when the
  * handle's mode is BCHOL_FP32_UPDATE). */
 bchol_status_t bchol_batch_set_precision(bchol_batch_t batch, int precision);
+
+/* bchol_batch_set_member_precision -- per-system precision modes for the next
+ * bchol_batch_plan (which then needs the same count): precision[m] is
+ * BCHOL_FP64 or BCHOL_FP64_SPLIT for system m (HOST array); count = 0 clears
+ * the override, and the batch's bchol_batch_set_precision mode applies to
+ * every system again.  One launch runs both kinds of systems.  For tuning the
+ * mode per class of systems (paper_2305_04635_gb300.autotune.tune_batch_classes).
+ * BCHOL_ERR_UNSUPPORTED for the FP32/TF32 modes, BCHOL_ERR_ARG otherwise. */
+bchol_status_t bchol_batch_set_member_precision(bchol_batch_t batch, int count, const int* precision);
 
 /* Schedule query of one system of a batch (host only): the batched kernel
  * walks each system's tasks in the ticket order of bchol_plan_task with tile

@@ -85,6 +85,7 @@ def load_library():
         "bchol_batch_plan": ([P, I, P, P, P, P, P, P, P, P, I, I], I),
         "bchol_batch_run": ([P, P], I),
         "bchol_batch_set_precision": ([P, I], I),
+        "bchol_batch_set_member_precision": ([P, I, P], I),
         "bchol_batch_solve_group": ([I, I, I, P, P, P], I),
         "bchol_batch_plan_task_count": ([I, I, I, I], ctypes.c_longlong),
         "bchol_batch_plan_task": ([I, I, I, I, ctypes.c_longlong, P, P, P, P], I),
@@ -351,10 +352,13 @@ class Batch:
     bands: list of band tensors (each (rows, n) with strides (1, ldab)), factored in place.
     ks:    half-bandwidths.  rhs: optional list of (n,) or (n, nrhs) column-major tensors
            (None entries = no solve for that system), overwritten by the solutions.
+    precision: FP64 or FP64_SPLIT for every system; member_precision: optional per-system modes
+           (one launch runs both kinds).
     The plan keeps the tensors' addresses: run() may be captured in a CUDA graph.
     """
 
-    def __init__(self, bands, ks, rhs=None, tile: int = 0, ctas_per_sm: int = 0, precision: int = FP64):
+    def __init__(self, bands, ks, rhs=None, tile: int = 0, ctas_per_sm: int = 0, precision: int = FP64,
+                 member_precision=None):
         lib = load_library()
         self._lib = lib
         count = len(bands)
@@ -384,6 +388,11 @@ class Batch:
         self._b = ctypes.c_void_p()
         _check("bchol_batch_create", lib.bchol_batch_create(ctypes.byref(self._b)))
         _check("bchol_batch_set_precision", lib.bchol_batch_set_precision(self._b, precision))
+        if member_precision is not None:
+            if len(member_precision) != count:
+                raise ValueError("member_precision must have one entry per system")
+            mp = A(*[int(x) for x in member_precision])
+            _check("bchol_batch_set_member_precision", lib.bchol_batch_set_member_precision(self._b, count, mp))
         _check("bchol_batch_plan", lib.bchol_batch_plan(
             self._b, count, ns, kk, ptrs, lds, ctypes.c_void_p(self.info.data_ptr()),
             nr if rhs is not None else None, bp if rhs is not None else None, ldb if rhs is not None else None,

@@ -361,7 +361,8 @@ struct bchol_batch_s {
   int b = 32;
   int ctas_per_sm = 1;
   int precision = BCHOL_FP64;   // BCHOL_FP64_SPLIT: updates as split products (tiles of 16 and 32)
-  bool split = false;           // the planned batch runs the split updates
+  std::vector<int> member_precision;   // per-system modes for the next plan (empty: `precision` for all)
+  bool split = false;           // some system of the planned batch runs the split updates
   bool any_rhs = false;
   int* info_dev = nullptr;
   size_t bytes = 0;
@@ -391,27 +392,42 @@ extern "C" bchol_status_t bchol_batch_set_precision(bchol_batch_t batch, int pre
   return BCHOL_OK;
 }
 
+extern "C" bchol_status_t bchol_batch_set_member_precision(bchol_batch_t batch, int count, const int* precision) {
+  if (!batch || count < 0 || (count > 0 && !precision)) return BCHOL_ERR_ARG;
+  for (int m = 0; m < count; ++m) {
+    if (precision[m] == BCHOL_FP32_UPDATE || precision[m] == BCHOL_TF32_UPDATE) return BCHOL_ERR_UNSUPPORTED;
+    if (precision[m] != BCHOL_FP64 && precision[m] != BCHOL_FP64_SPLIT) return BCHOL_ERR_ARG;
+  }
+  batch->member_precision.assign(precision, precision + count);
+  return BCHOL_OK;
+}
+
 extern "C" bchol_status_t bchol_batch_plan(bchol_batch_t batch, int count, const int* n, const int* k, double* const* ab,
                                            const int* ldab, int* info_dev, const int* nrhs, double* const* b,
                                            const int* ldb, int tile, int ctas_per_sm) {
   if (!batch || count <= 0 || !n || !k || !ab || !ldab || !info_dev) return BCHOL_ERR_ARG;
   if (!(tile == 0 || tile == 16 || tile == 32 || tile == 64) || ctas_per_sm < 0 || ctas_per_sm > 8) return BCHOL_ERR_ARG;
-  int kmax = 0;
   for (int m = 0; m < count; ++m) {
     if (n[m] < 1 || k[m] < 0 || ldab[m] < k[m] + 1 || !ab[m]) return BCHOL_ERR_ARG;
     const int r = nrhs ? nrhs[m] : 0;
     if (r < 0 || (r > 0 && (!b || !b[m] || !ldb || ldb[m] < n[m]))) return BCHOL_ERR_ARG;
-    kmax = std::max(kmax, std::min(k[m], n[m] - 1));
   }
-  const int bt = tile ? tile : (kmax <= 256 ? 16 : 32);
-  const bool split = batch->precision == BCHOL_FP64_SPLIT && (bt == 16 || bt == 32);
+  // automatic tile: 32 (tiles of 16 quadruple the tasks, and per-task latency bounds this launch)
+  const int bt = tile ? tile : 32;
+  if (!batch->member_precision.empty() && (int)batch->member_precision.size() != count) return BCHOL_ERR_ARG;
+  auto split_of = [&](int m) {
+    const int pm = batch->member_precision.empty() ? batch->precision : batch->member_precision[m];
+    return pm == BCHOL_FP64_SPLIT && (bt == 16 || bt == 32);
+  };
+  bool split = false;
   std::vector<BatchMat> mats(count);
   std::vector<double> work(count);
   size_t flag_total = 0;
   bool any_rhs = false;
   for (int m = 0; m < count; ++m) {
     const int kk = std::min(k[m], n[m] - 1);
-    const FactorPlan P = make_factor_plan(n[m], kk, bt, split);
+    const FactorPlan P = make_factor_plan(n[m], kk, bt, split_of(m));
+    split = split || P.H > 1;
     BatchMat& M = mats[m];
     M.ab = ab[m];
     M.ldab = ldab[m];
@@ -500,7 +516,7 @@ extern "C" bchol_status_t bchol_batch_plan(bchol_batch_t batch, int count, const
   batch->count = count;
   batch->b = bt;
   batch->split = split;
-  batch->ctas_per_sm = ctas_per_sm ? ctas_per_sm : (kmax < 1536 ? 1 : 2);
+  batch->ctas_per_sm = ctas_per_sm ? ctas_per_sm : 2;   // automatic: two (more hide more of the per-task latency)
   batch->any_rhs = any_rhs;
   batch->info_dev = info_dev;
   return BCHOL_OK;

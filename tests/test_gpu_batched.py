@@ -196,3 +196,55 @@ def test_factor_batched_uses_the_handle_precision():
         if B is not None:
             X = r.T.contiguous().cpu().numpy().T
             assert np.linalg.norm(X - oracle.pbtrs(Lref, k, B)) / np.linalg.norm(oracle.pbtrs(Lref, k, B)) <= TOL
+
+
+def test_batched_member_precision_matches_oracle():
+    """One launch with systems in both modes (FP64 FMA updates and split tensor-core strips)."""
+    probs, bands, rhs = _make(CASES, seed=17)
+    modes = [bchol.FP64 if m % 3 == 0 else SPLIT for m in range(len(CASES))]
+    batch = bchol.Batch(bands, [p[1] for p in probs], rhs, tile=32, ctas_per_sm=2, precision=SPLIT,
+                        member_precision=modes)
+    h = bchol.Handle()
+    rc, infos = bchol.get_info(batch.run(h), handle=h)
+    assert rc == 0 and infos == [0] * len(CASES)
+    for (n, k, A0, B), ab, r in zip(probs, bands, rhs):
+        Lref, _ = oracle.pbtrf(A0, k)
+        L = _band_cpu(ab)[: k + 1]
+        valid = ~g.unused_mask(k + 1, k, n)
+        assert np.linalg.norm((L - Lref)[valid]) / np.linalg.norm(Lref[valid]) <= TOL
+        if B is not None:
+            X = r.T.contiguous().cpu().numpy().T
+            Xref = oracle.pbtrs(Lref, k, B)
+            assert np.linalg.norm(X - Xref) / np.linalg.norm(Xref) <= TOL
+    with pytest.raises(ValueError):
+        bchol.Batch(bands, [p[1] for p in probs], rhs, member_precision=modes[:-1])
+
+
+def test_class_autotuner_caches_per_class_entries(tmp_path):
+    """tune_batch_classes picks the update mode per (n, k) class (in the context of the whole batch),
+    caches each timed class's decision, and the batch planned with its per-system modes matches the
+    oracle."""
+    import json
+    cases = [(600 + 37 * m, 40 + 9 * (m % 4), 0, 1) for m in range(10)] + \
+            [(900 + 41 * m, 150 + 13 * (m % 5), 0, 1) for m in range(10)]
+    probs, bands, rhs = _make(cases, seed=19)
+    ks = [p[1] for p in probs]
+    cache = str(tmp_path / "tune.json")
+    plan = autotune.tune_batch_classes(bands, ks, rhs, cache_path=cache)
+    assert set(plan["classes"]) == {autotune.k_class(k) for k in ks}
+    assert all(v in (bchol.FP64, SPLIT) for v in plan["classes"].values())
+    data = json.load(open(cache))
+    timed = {c for c in plan["classes"] if sum(autotune.k_class(k) == c for k in ks) >= 8}   # min_count
+    assert len(timed) == 2
+    assert {key.split("-t")[0][len("class-"):] for key in data if key.startswith("class-")} == timed
+    assert autotune.tune_batch_classes(bands, ks, rhs, cache_path=cache) == plan   # served from the cache
+    batch = bchol.Batch(bands, ks, rhs, tile=plan["tile"], ctas_per_sm=plan["ctas_per_sm"], precision=SPLIT,
+                        member_precision=plan["member_precision"])
+    h = bchol.Handle()
+    rc, infos = bchol.get_info(batch.run(h), handle=h)
+    assert rc == 0 and infos == [0] * len(cases)
+    for (n, k, A0, B), ab in zip(probs, bands):
+        Lref, _ = oracle.pbtrf(A0, k)
+        L = _band_cpu(ab)[: k + 1]
+        valid = ~g.unused_mask(k + 1, k, n)
+        assert np.linalg.norm((L - Lref)[valid]) / np.linalg.norm(Lref[valid]) <= TOL

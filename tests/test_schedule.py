@@ -254,3 +254,10 @@ def test_batched_strip_order_rejects_bad_arguments():
     assert lib.bchol_batch_plan_task_count(100, 10, 48, SPLIT) == -1
     assert lib.bchol_batch_plan_task_count(100, 10, 32, 1) == -1        # FP32_UPDATE has no batched form
     assert lib.bchol_batch_plan_task_count(100, 10, 32, SPLIT) > 0
+
+
+def test_k_classes_are_power_of_two_buckets():
+    from paper_2305_04635_gb300.autotune import k_class
+    assert k_class(0) == k_class(31) == "k0-32"
+    assert k_class(32) == k_class(63) == "k32-64"
+    assert k_class(64) == "k64-128" and k_class(400) == "k256-512" and k_class(2000) == "k1024-2048"
