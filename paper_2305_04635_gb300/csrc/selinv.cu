@@ -391,24 +391,27 @@ __device__ bool sel_diag(const SelArgs& a, int J, Smem<B>& sm, int* s_flag) {
   const int jmax = min(B, a.n - J * B);
   if (tid < B) s_rl[tid] = (tid < jmax) ? 1.0 / sL[tid * B + tid] : 0.0;   // every reciprocal at once
   __syncthreads();
-  // The recurrence is warp 0's alone (row i on lane i), so warp barriers order
-  // it; the other warps wait at the block barrier below.
+  // The recurrence is warp 0's alone (rows i = lane, lane + 32, ...), so warp
+  // barriers order it; the other warps wait at the block barrier below.
   if (tid < 32) {
     const int lane = tid;
     for (int j = jmax - 1; j >= 0; --j) {
       const double rl = s_rl[j];
       double part = 0.0;
-      if (lane > j && lane < jmax) {   // Sigma_ij for i > j
-        double s = sE[j * B + lane];
-        for (int mm = j + 1; mm < jmax; ++mm) s = fma(sL[j * B + mm], sS[mm * B + lane], s);   // L(mm,j) Sigma(i,mm)
-        const double v = -s * rl;
-        sS[j * B + lane] = v;
-        part = sL[j * B + lane] * v;   // L(i,j) Sigma(i,j)
+      for (int i = lane; i < jmax; i += 32) {
+        if (i > j) {   // Sigma_ij for i > j
+          double s = sE[j * B + i];
+          for (int mm = j + 1; mm < jmax; ++mm) s = fma(sL[j * B + mm], sS[mm * B + i], s);   // L(mm,j) Sigma(i,mm)
+          const double v = -s * rl;
+          sS[j * B + i] = v;
+          part = fma(sL[j * B + i], v, part);   // L(i,j) Sigma(i,j)
+        }
       }
 #pragma unroll
-      for (int off = B / 2; off >= 1; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);   // rows are lanes < B
+      for (int off = (B < 32 ? B : 32) / 2; off >= 1; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
       if (lane == 0) sS[j * B + j] = (rl - (sE[j * B + j] + part)) * rl;
-      if (lane > j && lane < jmax) sS[lane * B + j] = sS[j * B + lane];   // symmetric copy (row j)
+      for (int i = lane; i < jmax; i += 32)
+        if (i > j) sS[i * B + j] = sS[j * B + i];   // symmetric copy (row j)
       __syncwarp();
     }
   }

@@ -38,7 +38,8 @@ def _oracle_grad_band(A, k, b):
 
 
 @pytest.mark.parametrize("n,k,tile", [(300, 40, 16), (300, 40, 32), (257, 33, 32), (200, 10, 16), (100, 0, 16),
-                                      (64, 100, 32), (500, 70, 32), (1000, 130, 16), (777, 200, 32)])
+                                      (64, 100, 32), (500, 70, 32), (1000, 130, 16), (777, 200, 32),
+                                      (300, 40, 64), (257, 100, 64), (777, 200, 64), (50, 60, 64), (1000, 130, 64)])
 def test_backward_band_matches_oracle(n, k, tile):
     L0, A, B = g.problem(n, k, seed=n + k, diag="log1e3", exact=False)
     b = B[:, 0]
