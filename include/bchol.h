@@ -367,7 +367,10 @@ bchol_status_t bchol_plan_task_ex(int n, int k, int tile, int precision, long lo
  * terms of P_IJ = sum_M Sigma_IM L_MJ), 1 = NEAR(I, J) (Sigma_IJ and its share of
  * E_J), 2 = DIAG(J) (the diagonal tile); block columns J run from last to first
  * (the Takahashi recurrences of the inverse's band; the paper's interior-point
- * motivation, Sec. 1).  tile is 16, 32 or 64. */
+ * motivation, Sec. 1).  The order is the launch's combined order: CTA 0 runs
+ * NEAR(J+1, J) and DIAG(J) of every column itself (the chain), placed after the
+ * column's other NEAR tasks and before the far terms that read DIAG(J); the
+ * other tasks are tickets.  tile is 16, 32 or 64. */
 long long bchol_adjoint_plan_task_count(int n, int k, int tile);
 bchol_status_t bchol_adjoint_plan_task(int n, int k, int tile, long long ticket, int* type, int* J, int* I, int* g);
 
