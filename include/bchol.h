@@ -334,6 +334,17 @@ bchol_status_t bchol_set_ctas_per_sm(bchol_handle_t handle, int ctas_per_sm);
  * Returns BCHOL_ERR_ARG for other values. */
 bchol_status_t bchol_set_solve_path(bchol_handle_t handle, int path);
 
+/* bchol_set_tile_staging -- how the diagonal chain's prefetch warps copy the
+ * tiles A(s, s) and A(s, s-1) of each step into shared memory (tiles of 16
+ * and 32): 0 plain coalesced loads; 1 (default) TMA (cp.async.bulk.tensor box
+ * copies over the band viewed as a 2-D tensor with column stride ldab - 1, on
+ * an mbarrier), used where ldab is odd and > 1 and the driver encodes the
+ * tensor map, else the plain loads.  bchol_last_tile_staging returns 1 if the last
+ * bchol_factor's chain used TMA, 0 if not, -1 for a null handle.
+ * BCHOL_ERR_ARG for other values. */
+bchol_status_t bchol_set_tile_staging(bchol_handle_t handle, int tma);
+int bchol_last_tile_staging(bchol_handle_t handle);
+
 /* Test hook for the failure path.  While set to a tile (I, J) >= 0, the
  * factor kernel's waits on the ready flag of tile (I, J) (b x b tiles, block
  * row I, block column J, 0 <= I-J <= ceil(k/b)) get a target that is never

@@ -96,6 +96,8 @@ def load_library():
         "bchol_plan_task_ex": ([I, I, I, I, ctypes.c_longlong, P, P, P, P], I),
         "bchol_set_precision": ([P, I, I, ctypes.c_double], I),
         "bchol_set_solve_path": ([P, I], I),
+        "bchol_set_tile_staging": ([P, I], I),
+        "bchol_last_tile_staging": ([P], I),
         "bchol_last_refinement": ([P, P, P, P], I),
         "bchol_check_pivot_rcp": ([P, P, P, I], I),
         "bchol_check_split_product": ([P, I, I, P, I, P, I, P, I], I),
@@ -159,6 +161,14 @@ class Handle:
     def set_solve_path(self, path: int) -> None:
         """bchol_solve's FP64 algorithm: 0 automatic, 1 cluster chain, 2 partitioned (k <= 112)."""
         _check("bchol_set_solve_path", self._lib.bchol_set_solve_path(self._h, path))
+
+    def set_tile_staging(self, tma: int) -> None:
+        """0: the chain copies its tiles with plain loads; 1: with TMA where ldab is odd."""
+        _check("bchol_set_tile_staging", self._lib.bchol_set_tile_staging(self._h, int(tma)))
+
+    def last_tile_staging(self) -> int:
+        """1 if the last factorization's chain copied its tiles with TMA."""
+        return int(self._lib.bchol_last_tile_staging(self._h))
 
     def set_wait_limit_ms(self, ms: int) -> None:
         _check("bchol_set_wait_limit_ms", self._lib.bchol_set_wait_limit_ms(self._h, ms))

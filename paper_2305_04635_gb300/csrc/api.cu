@@ -48,6 +48,8 @@ struct bchol_handle_s {
   int last_iters = 0;
   double last_resid = 0.0, last_corr = 0.0;
   int solve_path = 0;  // 0 automatic, 1 cluster, 2 partitioned
+  int tma = 1;         // the chain's tile copies: 0 plain loads, 1 TMA where possible (measured no slower)
+  int last_tma = 0;    // whether the last factorization's chain used TMA
 };
 
 using namespace bchol;
@@ -231,6 +233,14 @@ bchol_status_t bchol_set_precision(bchol_handle_t h, bchol_precision_t precision
   return BCHOL_OK;
 }
 
+bchol_status_t bchol_set_tile_staging(bchol_handle_t h, int tma) {
+  if (!h || (tma != 0 && tma != 1)) return BCHOL_ERR_ARG;
+  h->tma = tma;
+  return BCHOL_OK;
+}
+
+int bchol_last_tile_staging(bchol_handle_t h) { return h ? h->last_tma : -1; }
+
 bchol_status_t bchol_set_solve_path(bchol_handle_t h, int path) {
   if (!h || path < 0 || path > 2) return BCHOL_ERR_ARG;
   h->solve_path = path;
@@ -383,7 +393,7 @@ bchol_status_t bchol_factor(bchol_handle_t h, int n, int k, double* ab, int ldab
   const FactorPlan P = make_factor_plan(n, kk, b, split);
   cudaError_t e = launch_factor(P, ab, ldab, info_dev, ws + kStatusBytes, status,
                                 (uint64_t)h->wait_ms * 1000000ull, h->ctas_per_sm ? h->ctas_per_sm : auto_ctas_per_sm(kk),
-                                h->stall_I, h->stall_J, h->stream);
+                                h->stall_I, h->stall_J, h->stream, h->tma, &h->last_tma);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return BCHOL_ERR_CUDA;

@@ -54,8 +54,11 @@ cudaError_t tc_ctas_per_sm(const void* func, size_t dyn_smem, int tmem_cols, int
 // Launch the persistent factor kernel.  `ws` holds factor_workspace_bytes()
 // bytes; `status` is a device int that outlives the call (timeout record).
 cudaError_t launch_pivot_rcp(const double* x, double* y, int n, cudaStream_t stream);
+// tma: the chain's prefetch warps copy their tiles with TMA where the band's
+// tensor map can be encoded (ldab odd); *tma_used (if given) reports whether they do.
 cudaError_t launch_factor(const FactorPlan& plan, double* ab, long long ldab, int* info, void* ws, int* status,
-                          uint64_t wait_ns, int ctas_per_sm, int stall_I, int stall_J, cudaStream_t stream);
+                          uint64_t wait_ns, int ctas_per_sm, int stall_I, int stall_J, cudaStream_t stream,
+                          int tma = 0, int* tma_used = nullptr);
 
 // Solve: block size and workspace of the inverted diagonal blocks.
 int solve_block(int k);

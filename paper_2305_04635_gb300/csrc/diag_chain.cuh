@@ -18,6 +18,8 @@
 // no compute warp stalls on a release), warps 5-7 wait for the next step's
 // input tiles and copy them into a second buffer while the current step runs.
 #pragma once
+#include <cuda.h>
+
 #include <type_traits>
 
 #include "factor_tasks.cuh"
@@ -89,6 +91,7 @@ struct DiagSmem {
   int fail;       // POTRF: first non-positive pivot (1-based column in the tile), or 0
   int ok;         // compute: broadcast of a wait result
   int pf_ok_d;    // prefetch: broadcast of the wait for A(s, s) and A(s, s-1)
+  unsigned long long pf_mbar;   // prefetch with TMA: completion of the two tile copies of a step
 };
 
 constexpr unsigned kPollNs = 64;  // back-off of the service warps' polls
@@ -187,16 +190,52 @@ __device__ void diag_publisher(const FactorArgs& a, DiagSmem<B, F32>& sm, int la
   }
 }
 
+// ------------------------------------------------ TMA copies of the two tiles
+// The band as a 2-D tensor: element (gi, gj) at ab + gi + gj (ldab - 1) (the
+// skewed tile view of bchol_device.cuh), dims (n, n), so that tile (I, J) is
+// the box at (I b, J b).  The whole view lies inside the n x ldab array; boxes
+// past n are zero-filled, slots outside the band are masked after the copy.
+// Used when (ldab - 1) * 8 is a multiple of 16 (ldab odd), the tensor-map rule.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void pf_mbar_init(unsigned long long* mb) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mb)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void pf_expect(unsigned long long* mb, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mb)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void pf_tma_2d(void* dst, const CUtensorMap* map, int x, int y, unsigned long long* mb) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(mb))
+      : "memory");
+}
+__device__ __forceinline__ bool pf_try_wait(unsigned long long* mb, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+      : "=r"(done)
+      : "r"(smem_u32(mb)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
 // ------------------------------------------------------- prefetcher (warps 5-7)
 // For step s: waits until the other CTAs have applied every update of A(s, s)
 // and A(s, s-1) except the step s-1 DSYRK (steps s0(s) .. s-2), and copies both
 // tiles into buffer s & 1 (free once step s-2 is finished).  One thread waits
 // for both (A(s, s-1) is the later one); the three warps copy both tiles with
 // all loads in flight at once.
+// With a.tma the copies are two TMA box loads onto an mbarrier (thread 0 of
+// the prefetcher issues them after the waits, the three warps wait for the
+// barrier with a bound, then zero the slots outside the band).
 template <int B, bool F32>
-__device__ void diag_prefetcher(const FactorArgs& a, DiagSmem<B, F32>& sm, int pt) {
+__device__ void diag_prefetcher(const FactorArgs& a, DiagSmem<B, F32>& sm, int pt, const CUtensorMap* tmap) {
   const uint64_t limit = 4 * a.wait_ns;
   bool failed = false;
+  if (a.tma && pt == 0) pf_mbar_init(&sm.pf_mbar);
+  bar_sync(kBarPF, 96);
   for (int s = 0; s < a.S; ++s) {
     const int cur = s & 1;
     const int s0 = first_step(a, s);
@@ -213,7 +252,43 @@ __device__ void diag_prefetcher(const FactorArgs& a, DiagSmem<B, F32>& sm, int p
       failed = true;
       break;
     }
-    load_tiles_group<B>(a, s, sm.D[cur], sm.X[cur], has_x, pt);
+    if (a.tma) {
+      if (pt == 0) {
+        // the buffer's previous contents were read (and masked) through the generic proxy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        pf_expect(&sm.pf_mbar, (has_x ? 2u : 1u) * B * B * 8u);
+        pf_tma_2d(sm.D[cur], tmap, s * B, s * B, &sm.pf_mbar);
+        if (has_x) pf_tma_2d(sm.X[cur], tmap, s * B, (s - 1) * B, &sm.pf_mbar);
+      }
+      const uint64_t t0 = globaltimer_ns();
+      bool ok;
+      while (!(ok = pf_try_wait(&sm.pf_mbar, (unsigned)(s & 1))) && globaltimer_ns() - t0 < limit) {
+      }
+      if (!ok) {   // a copy that never completes: record it and stop the chain (after a second bounded wait)
+        if (pt == 0) {
+          atomicExch(a.status, kStatusTimeout);
+          atomicExch(&a.ctl->abort, 1);
+          const uint64_t t1 = globaltimer_ns();
+          while (!pf_try_wait(&sm.pf_mbar, (unsigned)(s & 1)) && globaltimer_ns() - t1 < limit) {
+          }
+        }
+        failed = true;
+        break;
+      }
+      constexpr int E = (B * B + 95) / 96;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {   // the slots outside the band (and above the diagonal) read as zero
+        const int idx = pt + 96 * e;
+        if (idx < B * B) {
+          const int i = idx % B, j = idx / B;
+          const int dd = i - j;
+          if (dd < 0 || dd > a.k) sm.D[cur][idx] = 0.0;
+          if (has_x && B + dd > a.k) sm.X[cur][idx] = 0.0;
+        }
+      }
+    } else {
+      load_tiles_group<B>(a, s, sm.D[cur], sm.X[cur], has_x, pt);
+    }
     bar_sync(kBarPF, 96);
     if (pt == 0) st_release_cta(&sm.in_ready, s + 1);
   }
@@ -448,7 +523,7 @@ __device__ void diag_compute(const FactorArgs& a, DiagSmem<B, F32>& sm, int tid)
 
 // Entry of the chain CTA (all kThreads threads).
 template <int B, bool F32>
-__device__ void diag_chain(const FactorArgs& a, DiagSmem<B, F32>& sm) {
+__device__ void diag_chain(const FactorArgs& a, DiagSmem<B, F32>& sm, const CUtensorMap* tmap) {
   static_assert(B == 16 || B == 32, "the diagonal chain supports tiles of 16 and 32");
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
@@ -472,7 +547,7 @@ __device__ void diag_chain(const FactorArgs& a, DiagSmem<B, F32>& sm) {
   if (warp == 4) {
     diag_publisher<B, F32>(a, sm, lane);
   } else if (warp >= 5) {
-    diag_prefetcher<B, F32>(a, sm, tid - 160);
+    diag_prefetcher<B, F32>(a, sm, tid - 160, tmap);
   } else {
     diag_compute<B, F32>(a, sm, tid);
   }

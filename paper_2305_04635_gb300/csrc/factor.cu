@@ -36,7 +36,9 @@
 // helper waits for precedes, in the combined order, every task that waits for
 // it, so this walk cannot deadlock either.
 #include <algorithm>
+#include <cstdint>
 #include <cstdio>
+#include <cstring>
 
 #include "diag_chain.cuh"
 #include "strip_task.cuh"
@@ -79,7 +81,7 @@ __device__ void factor_helper(const FactorArgs& a, Smem<B>& sm, int* s_flag, int
 // 256 (tiles of 32) or 128 (tiles of 16) columns of tensor memory for its
 // lifetime.
 template <int B, bool F32, int MODE, bool TC>
-__global__ void __launch_bounds__(kThreads, 2) factor_kernel(FactorArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) factor_kernel(FactorArgs a, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ long long s_task;
   __shared__ int s_flag;
@@ -88,7 +90,7 @@ __global__ void __launch_bounds__(kThreads, 2) factor_kernel(FactorArgs a) {
   if constexpr (MODE >= 1) {
     if (blockIdx.x == 0) {
       if (threadIdx.x == 0) st_release(&a.ctl->chain_sm, sm_id() + 1);
-      diag_chain<B, F32>(a, *reinterpret_cast<DiagSmem<B, F32>*>(smem_raw));
+      diag_chain<B, F32>(a, *reinterpret_cast<DiagSmem<B, F32>*>(smem_raw), &tmap);
       return;
     }
     if constexpr (MODE == 2) {
@@ -224,7 +226,7 @@ cudaError_t tc_ctas_per_sm(const void* func, size_t dyn_smem, int tmem_cols, int
 }
 
 template <int B, bool F32, int MODE, bool TC = false>
-static cudaError_t launch_b(const FactorArgs& a, int ctas_per_sm, cudaStream_t stream) {
+static cudaError_t launch_b(const FactorArgs& a, const CUtensorMap& tmap, int ctas_per_sm, cudaStream_t stream) {
   size_t smem = sizeof(Smem<B>);
   if constexpr (MODE >= 1) smem = std::max(smem, sizeof(DiagSmem<B, F32>));
   if constexpr (TC) smem = std::max(smem, sizeof(split::Smem<B>));
@@ -258,12 +260,43 @@ static cudaError_t launch_b(const FactorArgs& a, int ctas_per_sm, cudaStream_t s
   const unsigned long long need = a.total + (MODE == 2 ? 3 : MODE == 1 ? 1 : 0);  // tickets + chain (+ helpers)
   if ((unsigned long long)grid > need) grid = (long long)need;
   if (grid < 1) grid = 1;
-  factor_kernel<B, F32, MODE, TC><<<(unsigned)grid, kThreads, smem, stream>>>(a);
+  factor_kernel<B, F32, MODE, TC><<<(unsigned)grid, kThreads, smem, stream>>>(a, tmap);
   return cudaGetLastError();
 }
 
+// The band as the 2-D tensor of the chain's TMA copies (diag_chain.cuh): element
+// (gi, gj) at ab + gi + gj (ldab - 1), dims (n, n), boxes of b x b.  False when
+// the tensor-map rules exclude it (stride (ldab - 1) * 8 not a multiple of 16,
+// a base not 16-byte aligned) or the driver declines the encoding.
+static bool encode_band_map(CUtensorMap* m, const double* ab, int n, long long ldab, int b) {
+  using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static Encode fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<Encode>(f);
+    else
+      cudaGetLastError();
+  }
+  if (!fn || ldab < 2 || ((ldab - 1) * 8) % 16 != 0 || (reinterpret_cast<uintptr_t>(ab) & 15) != 0) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)n};
+  const cuuint64_t strides[1] = {(cuuint64_t)(ldab - 1) * 8};
+  const cuuint32_t box[2] = {(cuuint32_t)b, (cuuint32_t)b};
+  const cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double*>(ab), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t launch_factor(const FactorPlan& P, double* ab, long long ldab, int* info, void* ws, int* status,
-                          uint64_t wait_ns, int ctas_per_sm, int stall_I, int stall_J, cudaStream_t stream) {
+                          uint64_t wait_ns, int ctas_per_sm, int stall_I, int stall_J, cudaStream_t stream,
+                          int tma, int* tma_used) {
   cudaError_t e = cudaMemsetAsync(info, 0, sizeof(int), stream);
   if (e != cudaSuccess || P.n <= 0) return e;
   e = cudaMemsetAsync(ws, 0, factor_workspace_bytes(P), stream);
@@ -291,23 +324,27 @@ cudaError_t launch_factor(const FactorPlan& P, double* ab, long long ldab, int* 
     a.Treg = P.helper ? P.Treg_hp : P.Treg_cp;
     a.total = P.helper ? P.total_hp : P.total_cp;
   }
+  CUtensorMap tmap;
+  memset(&tmap, 0, sizeof(tmap));
+  a.tma = (tma && P.b <= 32 && encode_band_map(&tmap, ab, P.n, ldab, P.b)) ? 1 : 0;
+  if (tma_used) *tma_used = a.tma;
   const bool h = P.helper;
   if (P.f32_update) {
     switch (P.b) {
-      case 16: return h ? launch_b<16, true, 2>(a, ctas_per_sm, stream) : launch_b<16, true, 1>(a, ctas_per_sm, stream);
-      case 32: return h ? launch_b<32, true, 2>(a, ctas_per_sm, stream) : launch_b<32, true, 1>(a, ctas_per_sm, stream);
-      case 64: return launch_b<64, true, 0>(a, ctas_per_sm, stream);
+      case 16: return h ? launch_b<16, true, 2>(a, tmap, ctas_per_sm, stream) : launch_b<16, true, 1>(a, tmap, ctas_per_sm, stream);
+      case 32: return h ? launch_b<32, true, 2>(a, tmap, ctas_per_sm, stream) : launch_b<32, true, 1>(a, tmap, ctas_per_sm, stream);
+      case 64: return launch_b<64, true, 0>(a, tmap, ctas_per_sm, stream);
       default: return cudaErrorInvalidValue;
     }
   }
   if (P.b == 32 && P.H > 1)
-    return h ? launch_b<32, false, 2, true>(a, ctas_per_sm, stream) : launch_b<32, false, 1, true>(a, ctas_per_sm, stream);
+    return h ? launch_b<32, false, 2, true>(a, tmap, ctas_per_sm, stream) : launch_b<32, false, 1, true>(a, tmap, ctas_per_sm, stream);
   if (P.b == 16 && P.H > 1)
-    return h ? launch_b<16, false, 2, true>(a, ctas_per_sm, stream) : launch_b<16, false, 1, true>(a, ctas_per_sm, stream);
+    return h ? launch_b<16, false, 2, true>(a, tmap, ctas_per_sm, stream) : launch_b<16, false, 1, true>(a, tmap, ctas_per_sm, stream);
   switch (P.b) {
-    case 16: return h ? launch_b<16, false, 2>(a, ctas_per_sm, stream) : launch_b<16, false, 1>(a, ctas_per_sm, stream);
-    case 32: return h ? launch_b<32, false, 2>(a, ctas_per_sm, stream) : launch_b<32, false, 1>(a, ctas_per_sm, stream);
-    case 64: return launch_b<64, false, 0>(a, ctas_per_sm, stream);
+    case 16: return h ? launch_b<16, false, 2>(a, tmap, ctas_per_sm, stream) : launch_b<16, false, 1>(a, tmap, ctas_per_sm, stream);
+    case 32: return h ? launch_b<32, false, 2>(a, tmap, ctas_per_sm, stream) : launch_b<32, false, 1>(a, tmap, ctas_per_sm, stream);
+    case 64: return launch_b<64, false, 0>(a, tmap, ctas_per_sm, stream);
     default: return cudaErrorInvalidValue;
   }
 }

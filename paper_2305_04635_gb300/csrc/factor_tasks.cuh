@@ -21,6 +21,7 @@ struct FactorArgs {
   uint64_t wait_ns;
   int stall;  // flag index whose waits never succeed (failure-path test hook), or -1
   int H;      // strip height of the ticket order (1: one tile per update task)
+  int tma = 0;  // the chain's prefetch warps copy A(s, s), A(s, s-1) with TMA (the kernel's tensor map)
 };
 
 __device__ __forceinline__ int fidx(const FactorArgs& a, int I, int J) { return J * (a.p + 1) + (I - J); }

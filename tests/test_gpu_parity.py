@@ -261,3 +261,34 @@ def test_partitioned_solve_at_full_size(k):
     ex = float(np.linalg.norm(X[:, 0] - xref) / np.linalg.norm(xref))
     print(f"partitioned n={n} k={k}: rel err x {ex:.2e}")
     assert ex <= TOL_X
+
+
+@pytest.mark.parametrize("staging", [0, 1])
+@pytest.mark.parametrize("tile", [16, 32])
+@pytest.mark.parametrize("n,k,extra,diag", CASES)
+def test_tile_staging_matches_oracle(n, k, extra, diag, tile, staging):
+    """The diagonal chain's tiles copied by plain loads (bchol_set_tile_staging(0)) or by TMA (1,
+    the default: used when ldab is odd and > 1, the tensor map's stride rule, plain loads
+    otherwise); the unused band slots hold NaN, so a slot outside the band that the copy's mask
+    missed would poison L."""
+    L0, A0, B = g.problem(n, k, seed=n + 7 * k, diag=diag, exact=False, nrhs=2)
+    ldab = k + 1 + extra
+    A = g.embed(A0, ldab, fill=np.nan)
+    h = bchol.Handle(tile=tile)
+    h.set_tile_staging(staging)
+    rc, info, L, X = run(A, k, B, handle=h, ldb_pad=3)
+    assert rc == 0 and info == 0, (rc, info)
+    tma_possible = tile <= 32 and ldab % 2 == 1 and ldab > 1
+    assert h.last_tile_staging() == (1 if staging and tma_possible else 0)
+    Lref, _ = oracle.pbtrf(A0, k)
+    assert np.all(np.isnan(L[g.unused_mask(ldab, k, n)]))
+    eL = rel_band_err(L, Lref, k)
+    ex = float(np.linalg.norm(X - oracle.pbtrs(Lref, k, B)) / np.linalg.norm(oracle.pbtrs(Lref, k, B)))
+    assert eL <= TOL_L and ex <= TOL_X
+
+
+def test_tile_staging_arguments():
+    h = bchol.Handle()
+    with pytest.raises(bchol.BcholError):
+        h.set_tile_staging(2)
+    assert h.last_tile_staging() == 0   # nothing factored yet
