@@ -715,6 +715,30 @@ def batched_case(count: int, n_scale: int, nrhs: int, precision: int, n: int = 0
     return {"case": "batched", "systems": len(ns), "n_scale": n_scale, "nrhs": nrhs, "ms": times}
 
 
+def adjoint_case(n: int, k: int, reps: int = 3) -> dict:
+    """The adjoint for profiling: factor and solve once, then `reps` backward calls (the solve of
+    bbar, the selected inversion, the gradient), each timed with CUDA events."""
+    import paper_2305_04635_gb300 as bchol
+    from paper_2305_04635_gb300.autograd import backward
+
+    A = bandgen.band_product(bandgen.l0_band(n, k, 0, "log1e3", exact=False), k)
+    L = bchol.band_from_numpy(A)
+    h = bchol.Handle()
+    bchol.factor(L, k, handle=h)
+    x = torch.from_numpy(bandgen.rhs(n, 1, 0)[:, 0].copy()).cuda()
+    bchol.solve(L, k, x, handle=h)
+    times = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0, e1 = _ev()
+        e0.record()
+        backward(L, k, x, x.clone(), 1.0, handle=h)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(round(e0.elapsed_time(e1), 3))
+    return {"case": "adjoint", "n": n, "k": k, "backward_ms": times}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -730,9 +754,10 @@ def main():
     ap.add_argument("--peaks", action="store_true", help="only measure the FP64/FP32/tensor unit rates and exit")
     ap.add_argument("--precision", default="split", choices=sorted(PRECISIONS),
                     help="trailing-update arithmetic: FP64 FMA, or FP64-accurate split products on the tensor cores")
-    ap.add_argument("--case", default="", choices=["", "batched"],
+    ap.add_argument("--case", default="", choices=["", "batched", "adjoint"],
                     help="only run a small case for profiling and print its times (batched: --count systems of the "
-                         "batch leg's draw with n divided by --n-scale, or one system with --system n,k)")
+                         "batch leg's draw with n divided by --n-scale, or one system with --system n,k; adjoint: "
+                         "three backward calls at --system n,k, default 20000,200)")
     ap.add_argument("--count", type=int, default=96)
     ap.add_argument("--n-scale", type=int, default=4)
     ap.add_argument("--nrhs", type=int, default=0)
@@ -765,6 +790,11 @@ def main():
         print(json.dumps(out))
         return
 
+    if args.case == "adjoint":
+        torch.cuda.set_device(local)
+        n, k = args.system if args.system else (20000, 200)
+        print(json.dumps(adjoint_case(n, k)))
+        return
     if args.case == "batched":
         torch.cuda.set_device(local)
         n, k = args.system if args.system else (0, 0)
