@@ -95,24 +95,38 @@ __device__ __forceinline__ FactorArgs matrix_args(const BatchArgs& g, int m) {
   return a;
 }
 
-// Are the inputs of task (type, s, I, J) final?  The same targets as the waits in the tasks.
+// Are the inputs of task (type, s, I, J) final?  The same targets as the waits
+// in the tasks.  A probe only: relaxed loads, all in flight together (the task
+// itself then waits with acquire ordering, and finds them met).
 __device__ __forceinline__ bool task_ready(const FactorArgs& a, int type, int s, int I, int J) {
   if (type == kStrip) {  // STRIP(I, J, s): every tile's panel tile and previous update, and L_Js
     const int h = strip_rows(a.H, s, min(a.p, a.S - 1 - s), I);
-    for (int t = 0; t < h; ++t) {
-      const int Ii = I + t, s0 = first_step(a, Ii);
-      if (ld_acquire(&a.flags[fidx(a, Ii, s)]) < s - s0 + 1 || ld_acquire(&a.flags[fidx(a, Ii, J)]) < s - s0)
-        return false;
+    int v[2 * 8 + 1], t[2 * 8 + 1];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const bool on = q < h;
+      const int Ii = I + (on ? q : 0), s0 = first_step(a, Ii);
+      v[2 * q] = on ? ld_relaxed(&a.flags[fidx(a, Ii, s)]) : 0;
+      t[2 * q] = on ? s - s0 + 1 : 0;
+      v[2 * q + 1] = on ? ld_relaxed(&a.flags[fidx(a, Ii, J)]) : 0;
+      t[2 * q + 1] = on ? s - s0 : 0;
     }
-    return (J >= I && J < I + h) || ld_acquire(&a.flags[fidx(a, J, s)]) >= s - first_step(a, J) + 1;
+    const bool own = J >= I && J < I + h;
+    v[16] = own ? 0 : ld_relaxed(&a.flags[fidx(a, J, s)]);
+    t[16] = own ? 0 : s - first_step(a, J) + 1;
+    bool ready = true;
+#pragma unroll
+    for (int q = 0; q < 17; ++q) ready = ready && v[q] >= t[q];
+    return ready;
   }
-  if (type == kPotrf) return ld_acquire(&a.flags[fidx(a, s, s)]) >= s - first_step(a, s);
-  if (type == kTrsm)
-    return ld_acquire(&a.flags[fidx(a, s, s)]) >= s - first_step(a, s) + 1 &&
-           ld_acquire(&a.flags[fidx(a, I, s)]) >= s - first_step(a, I);
-  return ld_acquire(&a.flags[fidx(a, I, s)]) >= s - first_step(a, I) + 1 &&
-         ld_acquire(&a.flags[fidx(a, J, s)]) >= s - first_step(a, J) + 1 &&
-         ld_acquire(&a.flags[fidx(a, I, J)]) >= s - first_step(a, I);
+  if (type == kPotrf) return ld_relaxed(&a.flags[fidx(a, s, s)]) >= s - first_step(a, s);
+  if (type == kTrsm) {
+    const int v0 = ld_relaxed(&a.flags[fidx(a, s, s)]), v1 = ld_relaxed(&a.flags[fidx(a, I, s)]);
+    return v0 >= s - first_step(a, s) + 1 && v1 >= s - first_step(a, I);
+  }
+  const int v0 = ld_relaxed(&a.flags[fidx(a, I, s)]), v1 = ld_relaxed(&a.flags[fidx(a, J, s)]),
+            v2 = ld_relaxed(&a.flags[fidx(a, I, J)]);
+  return v0 >= s - first_step(a, I) + 1 && v1 >= s - first_step(a, J) + 1 && v2 >= s - first_step(a, I);
 }
 
 template <int B, bool TC>

@@ -34,6 +34,41 @@ __device__ __forceinline__ bool wait_tile(const FactorArgs& a, int I, int J, int
   return wait_flag_geq(&a.flags[f], target, a.ctl, a.status, a.wait_ns);
 }
 
+// Wait (one thread) until each of the cnt ready counters f[q] (flag indices)
+// reaches t[q].  From three counters on (the strips), they are read with
+// relaxed loads, all in flight together, and one acquire fence follows when
+// every target is met: one L2 round trip where acquire loads one after another
+// would take cnt (an acquire load holds back the memory operations after it).
+// Otherwise (one or two counters, where the GPU-scope fence costs about what it
+// saves), and for the test hook's stalled counter, the bounded waits of
+// wait_tile, one at a time.
+template <int N>
+__device__ __forceinline__ bool wait_tiles(const FactorArgs& a, const int (&f)[N], const int (&t)[N], int cnt) {
+  if (cnt <= 2) {
+    for (int q = 0; q < cnt; ++q) {
+      const int target = f[q] == a.stall ? 0x7fffffff : t[q];
+      if (!wait_flag_geq(&a.flags[f[q]], target, a.ctl, a.status, a.wait_ns)) return false;
+    }
+    return true;
+  }
+  int v[N];
+#pragma unroll
+  for (int q = 0; q < N; ++q) v[q] = q < cnt ? ld_relaxed(&a.flags[f[q]]) : 0;
+  bool met = true;
+#pragma unroll
+  for (int q = 0; q < N; ++q)
+    if (q < cnt && (v[q] < t[q] || f[q] == a.stall)) met = false;
+  if (met) {
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    return true;
+  }
+  for (int q = 0; q < cnt; ++q) {
+    const int target = f[q] == a.stall ? 0x7fffffff : t[q];
+    if (!wait_flag_geq(&a.flags[f[q]], target, a.ctl, a.status, a.wait_ns)) return false;
+  }
+  return true;
+}
+
 constexpr int kThreads = 256;
 
 template <int B>
@@ -134,8 +169,9 @@ __device__ bool task_trsm(const FactorArgs& a, int I, int s, Smem<B>& sm, int* s
   __shared__ double s_rinv[B];
   const int tid = threadIdx.x;
   if (tid == 0) {
-    bool ok = wait_tile(a, s, s, s - first_step(a, s) + 1);
-    if (ok) ok = wait_tile(a, I, s, s - first_step(a, I));
+    const int f[2] = {fidx(a, s, s), fidx(a, I, s)};
+    const int t[2] = {s - first_step(a, s) + 1, s - first_step(a, I)};
+    bool ok = wait_tiles(a, f, t, 2);
     *s_flag = ok;
   }
   __syncthreads();
@@ -195,8 +231,9 @@ __device__ bool task_upd(const FactorArgs& a, int I, int J, int s, Smem<B>& sm, 
   // last (for UPD(I, s+1, s) it is the diagonal chain's TRSM), so it is waited
   // for and loaded after the others are already in flight.
   if (tid == 0) {
-    bool ok = lis_in_smem || wait_tile(a, I, s, s - s0I + 1);
-    if (ok) ok = wait_tile(a, I, J, s - s0I);
+    const int f[2] = {fidx(a, I, J), fidx(a, I, s)};
+    const int t[2] = {s - s0I, s - s0I + 1};
+    bool ok = wait_tiles(a, f, t, lis_in_smem ? 1 : 2);
     *s_flag = ok;
   }
   __syncthreads();
@@ -275,8 +312,9 @@ __device__ bool task_trsm_f32(const FactorArgs& a, int I, int s, Smem<B>& sm, in
   __shared__ float s_rinv32[B];
   const int tid = threadIdx.x;
   if (tid == 0) {
-    bool ok = wait_tile(a, s, s, s - first_step(a, s) + 1);
-    if (ok) ok = wait_tile(a, I, s, s - first_step(a, I));
+    const int f[2] = {fidx(a, s, s), fidx(a, I, s)};
+    const int t[2] = {s - first_step(a, s) + 1, s - first_step(a, I)};
+    bool ok = wait_tiles(a, f, t, 2);
     *s_flag = ok;
   }
   __syncthreads();
@@ -336,8 +374,9 @@ __device__ bool task_upd_f32(const FactorArgs& a, int I, int J, int s, Smem<B>& 
   // As in task_upd: L_Is and A_IJ first, with their loads in flight while
   // L_Js is waited for; A_IJ goes straight to registers.
   if (tid == 0) {
-    bool ok = wait_tile(a, I, s, s - s0I + 1);
-    if (ok) ok = wait_tile(a, I, J, s - s0I);
+    const int f[2] = {fidx(a, I, s), fidx(a, I, J)};
+    const int t[2] = {s - s0I + 1, s - s0I};
+    bool ok = wait_tiles(a, f, t, 2);
     *s_flag = ok;
   }
   __syncthreads();

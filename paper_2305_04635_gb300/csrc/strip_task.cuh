@@ -19,14 +19,25 @@ __device__ bool task_strip(const FactorArgs& a, int I0, int J, int s, split::Sme
   const int ms = min(a.p, a.S - 1 - s);
   const int h = strip_rows(a.H, s, ms, I0);
   if (threadIdx.x == 0) {
-    bool ok = true;
-    for (int t = 0; t < h && ok; ++t) {
-      const int I = I0 + t, s0 = first_step(a, I);
-      ok = wait_tile(a, I, s, s - s0 + 1) && wait_tile(a, I, J, s - s0);
+    // every tile's panel tile and previous update, and L_Js (one of the strip's own
+    // panel tiles when the strip starts on the diagonal), read together
+    constexpr int N = 2 * (split::kRowsA / B) + 1;
+    int f[N], tg[N], cnt = 0;
+#pragma unroll
+    for (int t = 0; t < split::kRowsA / B; ++t) {
+      if (t < h) {
+        const int I = I0 + t, s0 = first_step(a, I);
+        f[cnt] = fidx(a, I, s);
+        tg[cnt++] = s - s0 + 1;
+        f[cnt] = fidx(a, I, J);
+        tg[cnt++] = s - s0;
+      }
     }
-    // L_Js is one of the strip's own panel tiles when the strip starts on the diagonal
-    if (ok && !(J >= I0 && J < I0 + h)) ok = wait_tile(a, J, s, s - first_step(a, J) + 1);
-    *s_flag = ok;
+    if (!(J >= I0 && J < I0 + h)) {
+      f[cnt] = fidx(a, J, s);
+      tg[cnt++] = s - first_step(a, J) + 1;
+    }
+    *s_flag = wait_tiles(a, f, tg, cnt);
   }
   __syncthreads();
   if (!*s_flag) return false;
