@@ -155,10 +155,12 @@ __global__ void __launch_bounds__(kThreads, 2) factor_batched_kernel(BatchArgs g
         unsigned long long t = 0;
         if (rd * 32 + lane < g.count) {
           Control* c = g.ctl + mm;
-          if (ld_relaxed(&c->retired) == 0) {
-            t = ld_relaxed_u64(&c->ticket);
+          const int retired = ld_relaxed(&c->retired);   // the three words in one round trip
+          t = ld_relaxed_u64(&c->ticket);
+          const int aborted = ld_relaxed(&c->abort);
+          if (retired == 0) {
             const FactorArgs a = matrix_args(g, mm);
-            if (t >= a.total || ld_relaxed(&c->abort) != 0) {
+            if (t >= a.total || aborted != 0) {
               if (atomicCAS(&c->retired, 0, 1) == 0) atomicAdd(g.retired, 1);
             } else {
               int type, s, I, J;
