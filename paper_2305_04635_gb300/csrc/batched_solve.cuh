@@ -328,7 +328,7 @@ __device__ __forceinline__ void sweep(Smem& sm, const Sys& m, double* bc, long l
     __syncthreads();
     if (G.W > 0 && tid == 128) {   // publish block I (all of its stores precede the barrier)
       __threadfence();
-      st_release(&G.ctl[0], (int)(base + t + 1));
+      st_relaxed(&G.ctl[0], (int)(base + t + 1));   // after the fence: the release pattern
     }
   }
 }
@@ -400,7 +400,7 @@ __device__ bool worker_sweep(WSmem& ws, const Sys& m, const double* bc, long lon
     __syncthreads();
     if (tid == 0) {
       __threadfence();
-      st_release(&G.ctl[32 + w], (int)(g + 1));
+      st_relaxed(&G.ctl[32 + w], (int)(g + 1));   // after the fence: the release pattern
     }
   }
   return true;

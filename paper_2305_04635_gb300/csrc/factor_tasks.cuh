@@ -77,12 +77,13 @@ struct Smem {
   double t1[B * B];
 };
 
-// Publish: every thread's stores are done (barrier), then one release store.
+// Publish: every thread's stores are done (barrier), then one fence and a
+// relaxed store of the counter (the release pattern, with a single fence).
 __device__ __forceinline__ void publish(int* flag, int value) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    st_release(flag, value);
+    st_relaxed(flag, value);
   }
 }
 

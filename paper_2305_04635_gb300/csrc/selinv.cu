@@ -403,8 +403,8 @@ __device__ bool sel_near(const SelArgs& a, int I, int J, Smem<B>& sm, int* s_fla
     for (int c = 0; c < R; ++c) out[(tx + 16 * c) * B + ty + 16 * r] = (ty + 16 * r >= tx + 16 * c) ? acc[r][c] : 0.0;
   __syncthreads();
   if (tid == 0) {
-    __threadfence();
-    st_release(sig_flag(a, I, J), 1);
+    __threadfence();   // then both counters (the release pattern, one fence)
+    st_relaxed(sig_flag(a, I, J), 1);
     atomicAdd(w_flag(a, J), 1);
   }
   return true;

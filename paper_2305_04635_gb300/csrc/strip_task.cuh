@@ -55,11 +55,11 @@ __device__ bool task_strip(const FactorArgs& a, int I0, int J, int s, split::Sme
   };
   if (!split::product<B>(sm, cx, la, lb, ldc, stc, a.wait_ns, a.status, &a.ctl->abort)) return false;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0) {   // one fence, then the tiles' counters (the release pattern)
     __threadfence();
     for (int t = 0; t < h; ++t) {
       const int I = I0 + t;
-      st_release(&a.flags[fidx(a, I, J)], s - first_step(a, I) + 1);
+      st_relaxed(&a.flags[fidx(a, I, J)], s - first_step(a, I) + 1);
     }
   }
   return true;
