@@ -36,6 +36,7 @@ constexpr int kSWarps = kSThreads / 32;
 constexpr int kQ = kSB / kSWarps;   // columns per warp in a 32 x 32 product
 constexpr int kMaxT = 6;            // far tiles per worker per round prefetched into shared memory
 constexpr int kRing = kMaxT + 1;    // pushed solution blocks kept per worker
+constexpr int kLd = kSB + 1;        // row pitch of a 32 x 32 block staged in shared memory
 constexpr size_t kBlk = (size_t)kSB * kSB;
 
 int solve_block(int) { return kSB; }
@@ -134,9 +135,14 @@ struct SolveArgs {
 };
 
 // Shared-memory layout (doubles).  The leader and the workers use different
-// parts of the union.  pfs/lvs are per-thread prefetch slots, double-buffered
-// by chain position, filled with cp.async: unlike plain loads, these copies do
-// not hold up the release of the cluster barrier at the end of a round.
+// parts of the union.  pfs/lvs hold 32 x 32 blocks, double-buffered by chain
+// position, filled with cp.async: unlike plain loads, these copies do not hold
+// up the release of the cluster barrier at the end of a round.  Entry (i, c)
+// of a product's matrix (i the output row, c the column) sits at c * kLd + i:
+// the consumer (lane = i) reads a row of consecutive words, and a copy whose
+// lanes run down a band column (the backward sweep's transposed tiles) writes
+// with a pitch of 33 words, so neither side has bank conflicts and every
+// global read is coalesced.
 // T is the arithmetic type of the sweeps: double for bchol_solve, float for
 // the correction solves of the mixed-precision refinement.  Band tiles and
 // the prepared blocks are always read as FP64 and rounded to T when used.
@@ -145,11 +151,11 @@ struct SolveSmem {
   union {
     T part[2][NW][NRC][kSB];             // leader: workers' shares for the next two blocks
     struct {
-      double pfs[2][kMaxT][kQ][kSThreads];  // worker: far band tiles
+      double pfs[2][kMaxT][kSB * kLd];    // worker: far band tiles
       T ring[kRing][NRC][kSB];             // worker: solution blocks pushed by the leader
     } w;
   } u;
-  double lvs[2][kQ][kSThreads];           // L_TT^{-1} (worker) or M_T / N_T (leader)
+  double lvs[2][kSB * kLd];               // L_TT^{-1} (worker) or M_T / N_T (leader)
   T red[kSWarps][NRC][kSB];
   T vec[NRC][kSB];                       // leader: last chain block; worker: its partial sum
 };
@@ -232,15 +238,19 @@ __global__ void __launch_bounds__(kSThreads, 1) solve_kernel(SolveArgs a) {
           const bool has = fwd ? (T >= 1) : (T + 1 < a.S);
           const double* cb = (fwd ? a.mfw : a.nbw) + (size_t)T * kBlk;
 #pragma unroll
-          for (int q = 0; q < kQ; ++q) cp_async8(&sm.lvs[buf][q][tid], has ? cb + (w + kSWarps * q) * kSB + lane : a.ab, has);
+          for (int q = 0; q < kQ; ++q) {
+            const int c = w + kSWarps * q;
+            cp_async8(&sm.lvs[buf][c * kLd + lane], has ? cb + c * kSB + lane : a.ab, has);
+          }
           cp_async_commit();
           return;
         }
         const double* li = a.linv + (size_t)T * kBlk;
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
-          const int c = w + kSWarps * q;   // forward: Linv(i, c) at [c*32+i]; backward: Linv(c, i) at [i*32+c]
-          cp_async8(&sm.lvs[buf][q][tid], li + (fwd ? c * kSB + lane : lane * kSB + c), true);
+          // the word at [x*32 + lane]: forward Linv(i = lane, c = x), backward Linv(c = lane, i = x)
+          const int x = w + kSWarps * q;
+          cp_async8(&sm.lvs[buf][fwd ? x * kLd + lane : lane * kLd + x], li + x * kSB + lane, true);
         }
         const int jlo = fwd ? max(0, T - a.P) : T + 2;
         const int jhi = fwd ? T - 2 : min(a.S - 1, T + a.P);
@@ -248,9 +258,12 @@ __global__ void __launch_bounds__(kSThreads, 1) solve_kernel(SolveArgs a) {
         for (int t = 0; t < kMaxT && J <= jhi; ++t, J += NW) {
 #pragma unroll
           for (int q = 0; q < kQ; ++q) {
+            // lanes run down a band column: forward i = lane, backward c = lane
+            const int x = w + kSWarps * q;
+            const int i = fwd ? lane : x, c = fwd ? x : lane;
             bool ok;
-            const double* src = tile_addr(a, fwd, T, J, lane, w + kSWarps * q, &ok);
-            cp_async8(&sm.u.w.pfs[buf][t][q][tid], src, ok);
+            const double* src = tile_addr(a, fwd, T, J, i, c, &ok);
+            cp_async8(&sm.u.w.pfs[buf][t][c * kLd + i], src, ok);
           }
         }
         cp_async_commit();
@@ -272,7 +285,7 @@ __global__ void __launch_bounds__(kSThreads, 1) solve_kernel(SolveArgs a) {
 #pragma unroll
           for (int q = 0; q < kQ; ++q) {
             const int c = w + kSWarps * q;
-            const VT m = (VT)((t < kMaxT) ? sm.u.w.pfs[buf][t][q][tid] : tile_entry(a, fwd, T, J, lane, c));
+            const VT m = (VT)((t < kMaxT) ? sm.u.w.pfs[buf][t][c * kLd + lane] : tile_entry(a, fwd, T, J, lane, c));
             const int gc = J * kSB + c;
 #pragma unroll
             for (int r = 0; r < NRC; ++r) {
@@ -297,7 +310,7 @@ __global__ void __launch_bounds__(kSThreads, 1) solve_kernel(SolveArgs a) {
           acc[r] = VT(0);
           if (r < nr) {
 #pragma unroll
-            for (int q = 0; q < kQ; ++q) acc[r] = fmat((VT)sm.lvs[buf][q][tid], sm.vec[r][w + kSWarps * q], acc[r]);
+            for (int q = 0; q < kQ; ++q) acc[r] = fmat((VT)sm.lvs[buf][(w + kSWarps * q) * kLd + lane], sm.vec[r][w + kSWarps * q], acc[r]);
           }
         }
         warp_sum_rows<NW, VT, NRC>(acc, nr, sm, w, lane);
@@ -330,7 +343,7 @@ __global__ void __launch_bounds__(kSThreads, 1) solve_kernel(SolveArgs a) {
             acc[r] = VT(0);
             if (r < nr) {
 #pragma unroll
-              for (int q = 0; q < kQ; ++q) acc[r] = fmat((VT)sm.lvs[buf][q][tid], sm.vec[r][w + kSWarps * q], acc[r]);
+              for (int q = 0; q < kQ; ++q) acc[r] = fmat((VT)sm.lvs[buf][(w + kSWarps * q) * kLd + lane], sm.vec[r][w + kSWarps * q], acc[r]);
             }
           }
           warp_sum_rows<NW, VT, NRC>(acc, nr, sm, w, lane);
