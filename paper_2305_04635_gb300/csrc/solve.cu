@@ -29,8 +29,6 @@ namespace cg = cooperative_groups;
 namespace bchol {
 
 constexpr int kSB = 32;        // solve block
-constexpr int kNRC = 8;        // right-hand sides per pass, FP64 sweeps
-constexpr int kNRC32 = 8;      // right-hand sides per pass, FP32 sweeps
 constexpr int kSThreads = 256;
 constexpr int kSWarps = kSThreads / 32;
 constexpr int kQ = kSB / kSWarps;   // columns per warp in a 32 x 32 product
@@ -369,10 +367,10 @@ __global__ void __launch_bounds__(kSThreads, 1) solve_kernel(SolveArgs a) {
   }
 }
 
+// Sets the launch attributes of one instantiation; false if its cluster size is refused.
 template <int CL, typename VT, int NRC>
-static cudaError_t launch_cluster(const SolveArgs& a0, cudaStream_t stream, bool* fits, bool need_all) {
-  SolveArgs a = a0;
-  a.use_ring = (a.P <= (CL - 1) * (kRing - 1)) ? 1 : 0;
+static cudaError_t prepare_kernel(bool* ok) {
+  *ok = true;
   const size_t smem = sizeof(SolveSmem<CL - 1, VT, NRC>);
   cudaError_t e = cudaFuncSetAttribute(solve_kernel<CL, VT, NRC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -380,14 +378,42 @@ static cudaError_t launch_cluster(const SolveArgs& a0, cudaStream_t stream, bool
     e = cudaFuncSetAttribute(solve_kernel<CL, VT, NRC>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) {
       cudaGetLastError();
-      *fits = false;
-      return cudaSuccess;
+      *ok = false;
     }
+  }
+  return cudaSuccess;
+}
+
+template <int CL, typename VT, int NRC>
+static cudaError_t launch_columns(cudaLaunchConfig_t cfg, const SolveArgs& a) {
+  bool ok = false;
+  cudaError_t e = prepare_kernel<CL, VT, NRC>(&ok);
+  if (e != cudaSuccess) return e;
+  if (!ok) return cudaErrorInvalidConfiguration;
+  cfg.dynamicSmemBytes = sizeof(SolveSmem<CL - 1, VT, NRC>);
+  return cudaLaunchKernelEx(&cfg, solve_kernel<CL, VT, NRC>, a);
+}
+
+// The cluster count comes from the 8-column instantiation (the largest shared
+// memory); the launch then takes the instantiation whose columns per pass
+// (1, 2, 4, 8) are the fewest that hold a cluster's share, so no product or
+// reduction loops over columns that are not there.
+template <int CL, typename VT>
+static cudaError_t launch_cluster(const SolveArgs& a0, cudaStream_t stream, bool* fits, bool need_all) {
+  constexpr int NRC = 8;
+  SolveArgs a = a0;
+  a.use_ring = (a.P <= (CL - 1) * (kRing - 1)) ? 1 : 0;
+  bool ok = false;
+  cudaError_t e = prepare_kernel<CL, VT, NRC>(&ok);
+  if (e != cudaSuccess) return e;
+  if (!ok) {
+    *fits = false;
+    return cudaSuccess;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(CL);
   cfg.blockDim = dim3(kSThreads);
-  cfg.dynamicSmemBytes = smem;
+  cfg.dynamicSmemBytes = sizeof(SolveSmem<CL - 1, VT, NRC>);
   cfg.stream = stream;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -408,10 +434,13 @@ static cudaError_t launch_cluster(const SolveArgs& a0, cudaStream_t stream, bool
   const int groups = (a.nrhs + a.rhs_per - 1) / a.rhs_per;
   cfg.gridDim = dim3(CL * groups);
   *fits = true;
-  return cudaLaunchKernelEx(&cfg, solve_kernel<CL, VT, NRC>, a);
+  if (a.rhs_per == 1) return launch_columns<CL, VT, 1>(cfg, a);
+  if (a.rhs_per == 2) return launch_columns<CL, VT, 2>(cfg, a);
+  if (a.rhs_per <= 4) return launch_columns<CL, VT, 4>(cfg, a);
+  return launch_columns<CL, VT, NRC>(cfg, a);
 }
 
-template <typename VT, int NRC>
+template <typename VT>
 static cudaError_t launch_solve_t(int n, int k, int nrhs, const double* ab, long long ldab, double* b, long long ldb,
                                   void* ws, int* launches, cudaStream_t stream) {
   *launches = 0;
@@ -431,10 +460,10 @@ static cudaError_t launch_solve_t(int n, int k, int nrhs, const double* ab, long
   bool fits = false;
   // One column per cluster when 16-CTA clusters can cover all of them; else 8-CTA
   // clusters (more of them fit); else 16-CTA clusters with several columns each.
-  e = launch_cluster<16, VT, NRC>(a, stream, &fits, true);
-  if (e == cudaSuccess && !fits) e = launch_cluster<8, VT, NRC>(a, stream, &fits, true);
-  if (e == cudaSuccess && !fits) e = launch_cluster<16, VT, NRC>(a, stream, &fits, false);
-  if (e == cudaSuccess && !fits) e = launch_cluster<8, VT, NRC>(a, stream, &fits, false);
+  e = launch_cluster<16, VT>(a, stream, &fits, true);
+  if (e == cudaSuccess && !fits) e = launch_cluster<8, VT>(a, stream, &fits, true);
+  if (e == cudaSuccess && !fits) e = launch_cluster<16, VT>(a, stream, &fits, false);
+  if (e == cudaSuccess && !fits) e = launch_cluster<8, VT>(a, stream, &fits, false);
   if (e == cudaSuccess && !fits) e = cudaErrorInvalidConfiguration;
   if (e == cudaSuccess) *launches = 2;
   return e;
@@ -450,12 +479,12 @@ cudaError_t launch_solve(int n, int k, int nrhs, const double* ab, long long lda
   const bool part_ok = kk >= 1 && kk <= psolve_max_k() && status != nullptr;
   const bool part = part_ok && (path == 2 || (path == 0 && n >= 8 * 256));
   if (part) return launch_psolve(n, kk, nrhs, ab, ldab, b, ldb, ws, status, wait_ns, launches, stream);
-  return launch_solve_t<double, kNRC>(n, k, nrhs, ab, ldab, b, ldb, ws, launches, stream);
+  return launch_solve_t<double>(n, k, nrhs, ab, ldab, b, ldb, ws, launches, stream);
 }
 
 cudaError_t launch_solve_f32(int n, int k, int nrhs, const double* ab, long long ldab, double* b, long long ldb,
                              void* ws, int* launches, cudaStream_t stream) {
-  return launch_solve_t<float, kNRC32>(n, k, nrhs, ab, ldab, b, ldb, ws, launches, stream);
+  return launch_solve_t<float>(n, k, nrhs, ab, ldab, b, ldb, ws, launches, stream);
 }
 
 }  // namespace bchol
