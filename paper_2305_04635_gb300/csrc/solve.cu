@@ -154,6 +154,7 @@ struct SolveSmem {
     } w;
   } u;
   double lvs[2][kSB * kLd];               // L_TT^{-1} (worker) or M_T / N_T (leader)
+  double bpre[2][NRC][kSB];               // worker 1: the block's right-hand side (b, or y backward)
   T red[kSWarps][NRC][kSB];
   T vec[NRC][kSB];                       // leader: last chain block; worker: its partial sum
 };
@@ -243,6 +244,12 @@ __global__ void __launch_bounds__(kSThreads, 1) solve_kernel(SolveArgs a) {
           cp_async_commit();
           return;
         }
+        if (rank == 1) {   // the block's b (y in the backward sweep): read before the leader overwrites it
+          for (int idx = tid; idx < nr * kSB; idx += kSThreads) {
+            const int r = idx / kSB, gi = T * kSB + idx % kSB;
+            cp_async8(&sm.bpre[buf][r][idx % kSB], gi < a.n ? bc + gi + (long long)r * a.ldb : a.ab, gi < a.n);
+          }
+        }
         const double* li = a.linv + (size_t)T * kBlk;
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
@@ -299,7 +306,7 @@ __global__ void __launch_bounds__(kSThreads, 1) solve_kernel(SolveArgs a) {
         for (int idx = tid; idx < nr * kSB; idx += kSThreads) {
           const int r = idx / kSB, i = idx % kSB;
           VT s = tree_sum<kSWarps, VT>(&sm.red[0][r][i], NRC * kSB);
-          if (rank == 1 && T * kSB + i < a.n) s -= (VT)__ldcg(bc + T * kSB + i + (long long)r * a.ldb);
+          if (rank == 1) s -= (VT)sm.bpre[buf][r][i];
           sm.vec[r][i] = s;
         }
         __syncthreads();
