@@ -58,9 +58,9 @@ SPLIT_MACS_PER_FMA = 28
 # DRAM bytes (read + write) of one factor launch at n = 20000 for each sweep k, from
 # an ncu capture of dram__bytes_read.sum + dram__bytes_write.sum of this kernel;
 # traffic is proportional to n at fixed k, so it is scaled by n / 20000.
-TRAFFIC_N20000 = {50: 8.5e6, 100: 16.9e6, 200: 35.5e6, 500: 105.3e6, 1000: 261.3e6, 2000: 567.8e6}
+TRAFFIC_N20000 = {50: 8.4e6, 100: 16.9e6, 200: 35.5e6, 500: 105.3e6, 1000: 258.5e6, 2000: 563.1e6}
 # The same for the launches with the split tensor-core updates (tile 32).
-TRAFFIC_SPLIT_N20000 = {1000: 257.3e6, 2000: 554.5e6}
+TRAFFIC_SPLIT_N20000 = {1000: 258.6e6, 2000: 555.7e6}
 
 
 def traffic_table(split: bool) -> dict:
