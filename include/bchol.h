@@ -326,11 +326,17 @@ bchol_status_t bchol_set_ctas_per_sm(bchol_handle_t handle, int ctas_per_sm);
 /* Algorithm of bchol_solve's FP64 sweeps (the result is the same to rounding):
  *   0  automatic (the default): partitioned for 1 <= k <= 112 and n >= 2048, else cluster
  *   1  cluster: the 32-row block chain on one thread-block cluster per group of
- *      right-hand sides, far blocks on the cluster's worker CTAs
+ *      right-hand sides, far blocks on the cluster's worker CTAs.  A one-column
+ *      solve with more than 16 blocks of band below the diagonal (k > 512) adds
+ *      up to 6 more 16-CTA clusters that take the block distances past 16 and
+ *      hand their sums over through the workspace, with waits bounded by the
+ *      handle's wait limit (a wait that runs out is reported by bchol_get_info
+ *      as BCHOL_ERR_TIMEOUT, and the solution is then not valid)
  *   2  partitioned (for 1 <= k <= 112; other k use the cluster path): chunks of
  *      256 rows solved independently, with k "spike" columns L_cc^{-1} L_{c,c-1}
  *      per chunk, a sequential pass over the chunks' k boundary values, and a
  *      second independent pass; n (k + nrhs) k multiply-adds per sweep
+ *   3  cluster as in 1, always on one cluster per group (no far clusters)
  * Returns BCHOL_ERR_ARG for other values. */
 bchol_status_t bchol_set_solve_path(bchol_handle_t handle, int path);
 

@@ -159,7 +159,8 @@ class Handle:
         return it.value, res.value, corr.value
 
     def set_solve_path(self, path: int) -> None:
-        """bchol_solve's FP64 algorithm: 0 automatic, 1 cluster chain, 2 partitioned (k <= 112)."""
+        """bchol_solve's FP64 algorithm: 0 automatic, 1 cluster chain (with far clusters for one
+        column at k > 512), 2 partitioned (k <= 112), 3 cluster chain on one cluster per group."""
         _check("bchol_set_solve_path", self._lib.bchol_set_solve_path(self._h, path))
 
     def set_tile_staging(self, tma: int) -> None:

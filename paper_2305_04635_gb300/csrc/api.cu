@@ -47,7 +47,7 @@ struct bchol_handle_s {
   const int* mixed_info = nullptr;
   int last_iters = 0;
   double last_resid = 0.0, last_corr = 0.0;
-  int solve_path = 0;  // 0 automatic, 1 cluster, 2 partitioned
+  int solve_path = 0;  // 0 automatic, 1 cluster, 2 partitioned, 3 cluster without far clusters
   int tma = 1;         // the chain's tile copies: 0 plain loads, 1 TMA where possible (measured no slower)
   int last_tma = 0;    // whether the last factorization's chain used TMA
 };
@@ -242,7 +242,7 @@ bchol_status_t bchol_set_tile_staging(bchol_handle_t h, int tma) {
 int bchol_last_tile_staging(bchol_handle_t h) { return h ? h->last_tma : -1; }
 
 bchol_status_t bchol_set_solve_path(bchol_handle_t h, int path) {
-  if (!h || path < 0 || path > 2) return BCHOL_ERR_ARG;
+  if (!h || path < 0 || path > 3) return BCHOL_ERR_ARG;
   h->solve_path = path;
   return BCHOL_OK;
 }

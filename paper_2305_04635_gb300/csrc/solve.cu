@@ -20,6 +20,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "bchol_device.cuh"
 #include "bchol_internal.h"
@@ -35,13 +36,21 @@ constexpr int kQ = kSB / kSWarps;   // columns per warp in a 32 x 32 product
 constexpr int kMaxT = 6;            // far tiles per worker per round prefetched into shared memory
 constexpr int kRing = kMaxT + 1;    // pushed solution blocks kept per worker
 constexpr int kLd = kSB + 1;        // row pitch of a 32 x 32 block staged in shared memory
+// Far clusters (one-column solves with more than 16 blocks of band below the
+// diagonal, 16-CTA clusters): the group's own cluster keeps the block
+// distances 2 .. 16 (one tile per worker) and up to kMaxF more clusters take
+// the distances beyond.
+constexpr int kMaxF = 6;            // far clusters per column group
+constexpr int kFarRing = 32;        // slots of the far partial sums (>= the near distances + 2)
+constexpr size_t kFarCtlBytes = 256;  // [0] positions published by the group, [1] abort, [8 + f] targets of far cluster f
 constexpr size_t kBlk = (size_t)kSB * kSB;
 
 int solve_block(int) { return kSB; }
 
 size_t solve_workspace_bytes(int n, int k) {
   const size_t S = (size_t)((n + kSB - 1) / kSB);
-  return std::max(3 * S * kBlk * sizeof(double), psolve_workspace_bytes(n, k));
+  const size_t cluster = 3 * S * kBlk * sizeof(double) + kFarCtlBytes + (size_t)kMaxF * kFarRing * kSB * sizeof(double);
+  return std::max(cluster, psolve_workspace_bytes(n, k));
 }
 
 // Band entry L(gi, gj) (zero outside the band or the matrix).
@@ -130,6 +139,12 @@ struct SolveArgs {
   const double* nbw;
   int use_ring;   // far solution blocks come from the pushed ring (else from global memory)
   int rhs_per;    // right-hand-side columns per cluster (clusters split the columns)
+  int far;        // far clusters per column group (0: none; only with one column per group)
+  int dnear;      // block distances 2 .. dnear on the group's own cluster (P without far clusters)
+  int* fctl;      // far-cluster control words (kFarCtlBytes, zeroed before the launch)
+  double* fsum;   // far partial sums: [far][kFarRing][kSB]
+  int* status;    // set to the timeout status if a bounded wait runs out
+  unsigned long long wait_ns;
 };
 
 // Shared-memory layout (doubles).  The leader and the workers use different
@@ -157,6 +172,9 @@ struct SolveSmem {
   double bpre[2][NRC][kSB];               // worker 1: the block's right-hand side (b, or y backward)
   T red[kSWarps][NRC][kSB];
   T vec[NRC][kSB];                       // leader: last chain block; worker: its partial sum
+  alignas(16) double fpre[2][kMaxF][kSB];  // worker 1: the far clusters' sums for the block
+  T fpart[2][NW + 1][kSB];                 // far cluster rank 0: the CTAs' partial sums of a target
+  int fseen;                               // worker 1: smallest far-cluster count seen so far
 };
 
 __device__ __forceinline__ double fmat(double a, double b, double c) { return fma(a, b, c); }
@@ -166,6 +184,29 @@ __device__ __forceinline__ void cp_async8(double* dst, const double* src, bool v
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   const int sz = valid ? 8 : 0;   // 0: nothing is read and the slot is zero-filled
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(sz) : "memory");
+}
+// 16-byte copy through L2 only (the far sums are rewritten by other clusters; no stale L1 line).
+__device__ __forceinline__ void cp_async16_cg(double* dst, const double* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+// One thread: wait until *flag >= target.  False when the group is aborted or
+// the wait runs out; a timeout sets the status word and the abort word, and the
+// caller goes on without waiting again (every CTA still takes all of its
+// cluster barriers, so nothing hangs; the result is then wrong and the status
+// says so).
+__device__ __forceinline__ bool far_wait(const SolveArgs& a, const int* flag, int target) {
+  if (ld_acquire(flag) >= target) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (true) {
+    if (ld_acquire(flag) >= target) return true;
+    if (ld_relaxed(&a.fctl[1]) != 0) return false;
+    if (globaltimer_ns() - t0 > a.wait_ns) {
+      atomicExch(a.status, kStatusTimeout);
+      atomicExch(&a.fctl[1], 1);
+      return false;
+    }
+  }
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
@@ -206,7 +247,132 @@ __device__ __forceinline__ const double* tile_addr(const SolveArgs& a, bool fwd,
   return *ok ? a.ab + d + (long long)gj * a.ldab : a.ab;
 }
 
+// A far cluster of a one-column group: for every target block T of both
+// sweeps, the sum over its block distances d = D0 + e, D0 + e + stride, ...
+// (D0 = dnear + 1, e = this CTA's index among the far clusters' CTAs) of
+//   forward  L_{T,T-d} y_{T-d},   backward  L_{T+d,T}^T x_{T+d},
+// summed over the cluster's CTAs through rank 0's shared memory and written to
+// slot g % kFarRing of the cluster's far sums; its count (the targets done)
+// goes out with the next target, and after the sweep's last one.  The
+// solved blocks come from the column itself (the leader stores each block
+// there) once the group's published count covers them; the band tiles come
+// one target ahead through cp.async.  Targets at positions below D0 have no
+// far terms.  Every CTA takes the same cluster barriers whatever happens to
+// its waits, so an abort ends in a wrong result and the status word, not a hang.
+// The cluster runs behind the chain's count in steady state, so it keeps the
+// last count it acquired and polls only when that falls short, and loads the
+// next target's blocks into registers while the current one is multiplied
+// (L2 loads: the column is rewritten between the sweeps).  Not inlined: the
+// chain cluster's code stays as compact as without far clusters.
 template <int CL, typename VT, int NRC>
+__device__ __noinline__ void far_cluster(const SolveArgs& a, SolveSmem<CL - 1, VT, NRC>& sm, cg::cluster_group& cluster, int f,
+                            int cbeg, int cend) {
+  constexpr int NW = CL - 1;
+  __shared__ int s_ok, s_seen;
+  const int rank = (int)cluster.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  SolveSmem<NW, VT, NRC>* root = cluster.map_shared_rank(&sm, 0);
+  const int D0 = a.dnear + 1, e = f * CL + rank, stride = a.far * CL;
+  bool alive = true;
+  if (tid == 0) s_seen = 0;
+  for (int c0 = cbeg; c0 < cend; c0 += NRC) {
+    const double* bc = a.b + (long long)c0 * a.ldb;
+    for (int sweep = 0; sweep < 2; ++sweep) {
+      const bool fwd = (sweep == 0);
+      const long long base = ((long long)((c0 - cbeg) / NRC) * 2 + sweep) * a.S;
+      auto tiles_at = [&](int pos) {   // this CTA's far tiles of the target at position pos
+        int nt = 0;
+        while (nt < kMaxT && D0 + e + nt * stride <= min(a.P, pos)) ++nt;
+        return nt;
+      };
+      auto prefetch = [&](int pos) {
+        if (pos >= a.S) return;
+        const int T = fwd ? pos : a.S - 1 - pos;
+        const int buf = pos & 1, nt = tiles_at(pos);
+        for (int t = 0; t < nt; ++t) {
+          const int d = D0 + e + t * stride, J = fwd ? T - d : T + d;
+#pragma unroll
+          for (int q = 0; q < kQ; ++q) {
+            const int x = w + kSWarps * q;
+            const int i = fwd ? lane : x, c = fwd ? x : lane;
+            bool ok;
+            const double* src = tile_addr(a, fwd, T, J, i, c, &ok);
+            cp_async8(&sm.u.w.pfs[buf][t][c * kLd + i], src, ok);
+          }
+        }
+        cp_async_commit();
+      };
+      // thread idx < nt * kSB holds block entry (t, c) = (idx / kSB, idx % kSB) of a target
+      auto yload = [&](int pos, int idx) {
+        const int T = fwd ? pos : a.S - 1 - pos;
+        const int t = idx / kSB, c = idx % kSB;
+        const int d = D0 + e + t * stride, gc = (fwd ? T - d : T + d) * kSB + c;
+        return gc < a.n ? __ldcg(bc + gc) : 0.0;
+      };
+      double ynext = 0.0;
+      bool have_next = false;
+      prefetch(D0);
+      for (int pos = D0; pos < a.S; ++pos) {
+        const int buf = pos & 1, nt = tiles_at(pos);
+        const long long g = base + pos;
+        cp_async_wait_all();
+        prefetch(pos + 1);
+        // the newest block read, at position pos - D0, is published once the count passes
+        // it.  Every CTA waits, tiles or not: the wait also keeps the cluster from writing
+        // slot g % kFarRing before worker 1 has copied the target kFarRing steps back.
+        if (tid == 0) {
+          int ok = alive ? 1 : 0;
+          if (ok && s_seen < (int)(g - D0 + 1)) {
+            ok = far_wait(a, &a.fctl[0], (int)(g - D0 + 1));
+            s_seen = ld_acquire(&a.fctl[0]);   // an acquire: the cached count covers later reads too
+          }
+          s_ok = ok;
+        }
+        __syncthreads();
+        alive = alive && s_ok;
+        if (tid < nt * kSB) sm.u.w.ring[tid / kSB][0][tid % kSB] = (VT)(have_next ? ynext : yload(pos, tid));
+        // the next target's blocks, if the count acquired so far covers them
+        have_next = pos + 1 < a.S && s_seen >= (int)(g + 1 - D0 + 1);
+        if (have_next && tid < tiles_at(pos + 1) * kSB) ynext = yload(pos + 1, tid);
+        __syncthreads();
+        VT acc = VT(0);
+        for (int t = 0; t < nt; ++t) {
+#pragma unroll
+          for (int q = 0; q < kQ; ++q) {
+            const int c = w + kSWarps * q;
+            acc = fmat((VT)sm.u.w.pfs[buf][t][c * kLd + lane], sm.u.w.ring[t][0][c], acc);
+          }
+        }
+        sm.red[w][0][lane] = acc;
+        __syncthreads();
+        if (tid < kSB) root->fpart[pos & 1][rank][tid] = tree_sum<kSWarps, VT>(&sm.red[0][0][tid], NRC * kSB);
+        cluster.sync();
+        if (rank == 0 && tid < kSB) {
+          // the count of the targets before this one goes out first: their sums were stored a
+          // target ago, so the fence has nothing left to wait for and stays off the path
+          if (tid == 0 && pos > D0) {
+            __threadfence();   // then the count: the release pattern (warp 0 stored the sums)
+            st_relaxed(&a.fctl[8 + f], (int)g);
+          }
+          a.fsum[((size_t)f * kFarRing + (size_t)(g % kFarRing)) * kSB + tid] =
+              (double)tree_sum<CL, VT>(&sm.fpart[pos & 1][0][tid], kSB);
+        }
+      }
+      if (rank == 0 && a.S > D0) {   // the sweep's last target
+        __syncthreads();
+        if (tid == 0) {
+          __threadfence();
+          st_relaxed(&a.fctl[8 + f], (int)(base + a.S));
+        }
+      }
+    }
+  }
+  cp_async_wait_all();
+}
+
+// FAR: the instantiation with the far-cluster roles (16-CTA clusters, FP64, one
+// column); the others carry none of that code.
+template <int CL, typename VT, int NRC, bool FAR = false>
 __global__ void __launch_bounds__(kSThreads, 1) solve_kernel(SolveArgs a) {
   constexpr int NW = CL - 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -216,15 +382,28 @@ __global__ void __launch_bounds__(kSThreads, 1) solve_kernel(SolveArgs a) {
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   SolveSmem<NW, VT, NRC>* leader = cluster.map_shared_rank(&sm, 0);
 
-  // Clusters split the right-hand sides: cluster blockIdx.x / CL takes columns
-  // [cid * rhs_per, (cid + 1) * rhs_per); the clusters run side by side.
-  const int cid = blockIdx.x / CL;
-  const int cbeg = cid * a.rhs_per, cend = min(a.nrhs, cbeg + a.rhs_per);
+  // Clusters split the right-hand sides: group grp = cluster / (1 + far) takes
+  // columns [grp * rhs_per, (grp + 1) * rhs_per); the groups run side by side.
+  // Within a group, cluster 0 runs the chain (the leader and its workers) and
+  // clusters 1 .. far the far distances (far > 0 only with one column a group).
+  const int ncl = FAR ? 1 + a.far : 1;
+  const int cid = blockIdx.x / CL, fidx = cid % ncl, grp = cid / ncl;
+  const int cbeg = grp * a.rhs_per, cend = min(a.nrhs, cbeg + a.rhs_per);
+  if constexpr (FAR) {
+    if (fidx > 0) {
+      far_cluster<CL, VT, NRC>(a, sm, cluster, fidx - 1, cbeg, cend);
+      return;
+    }
+  }
+  constexpr bool far_on = FAR;
+  const int pn = far_on ? a.dnear : a.P;   // the largest block distance this cluster's workers take
+  if (rank == 1 && tid == 0) sm.fseen = 0;
   for (int c0 = cbeg; c0 < cend; c0 += NRC) {
     const int nr = min(NRC, cend - c0);
     double* bc = a.b + (long long)c0 * a.ldb;
     for (int sweep = 0; sweep < 2; ++sweep) {
       const bool fwd = (sweep == 0);
+      const long long base = ((long long)((c0 - cbeg) / NRC) * 2 + sweep) * a.S;
       for (int idx = tid; idx < NRC * kSB; idx += kSThreads) (&sm.vec[0][0])[idx] = VT(0);
       // Registers prefetched one round ahead: the worker's far tiles and L_TT^{-1} (or its
       // transpose), or the leader's coupling block M_T / N_T.  Lane = output row i, column
@@ -249,6 +428,25 @@ __global__ void __launch_bounds__(kSThreads, 1) solve_kernel(SolveArgs a) {
             const int r = idx / kSB, gi = T * kSB + idx % kSB;
             cp_async8(&sm.bpre[buf][r][idx % kSB], gi < a.n ? bc + gi + (long long)r * a.ldb : a.ab, gi < a.n);
           }
+          if (far_on && pos > a.dnear && w == 0) {
+            // the far clusters' sums for this block: each lane acquires the counts itself
+            // (bounded), unless an earlier look already saw them past this target
+            const int g = (int)(base + pos);
+            if (sm.fseen < g + 1) {
+              int seen = 0x7fffffff;
+              for (int f = 0; f < a.far; ++f) {
+                far_wait(a, &a.fctl[8 + f], g + 1);
+                seen = min(seen, ld_acquire(&a.fctl[8 + f]));   // acquired: later targets read under it
+              }
+              __syncwarp();
+              if (lane == 0) sm.fseen = seen;
+              __syncwarp();
+            }
+            for (int idx = lane; idx < a.far * (kSB / 2); idx += 32) {
+              const int f = idx / (kSB / 2), h = 2 * (idx % (kSB / 2));
+              cp_async16_cg(&sm.fpre[buf][f][h], a.fsum + ((size_t)f * kFarRing + (size_t)(g % kFarRing)) * kSB + h);
+            }
+          }
         }
         const double* li = a.linv + (size_t)T * kBlk;
 #pragma unroll
@@ -257,8 +455,8 @@ __global__ void __launch_bounds__(kSThreads, 1) solve_kernel(SolveArgs a) {
           const int x = w + kSWarps * q;
           cp_async8(&sm.lvs[buf][fwd ? x * kLd + lane : lane * kLd + x], li + x * kSB + lane, true);
         }
-        const int jlo = fwd ? max(0, T - a.P) : T + 2;
-        const int jhi = fwd ? T - 2 : min(a.S - 1, T + a.P);
+        const int jlo = fwd ? max(0, T - pn) : T + 2;
+        const int jhi = fwd ? T - 2 : min(a.S - 1, T + pn);
         int J = jlo + ((rank - 1) - (jlo % NW) + NW) % NW;
         for (int t = 0; t < kMaxT && J <= jhi; ++t, J += NW) {
 #pragma unroll
@@ -278,8 +476,8 @@ __global__ void __launch_bounds__(kSThreads, 1) solve_kernel(SolveArgs a) {
       //   backward L_TT^{-T} (sum_J L_JT^T x_J [- y_T for worker 1])
       auto worker_step = [&](int pos) {
         const int T = fwd ? pos : a.S - 1 - pos;
-        const int jlo = fwd ? max(0, T - a.P) : T + 2;
-        const int jhi = fwd ? T - 2 : min(a.S - 1, T + a.P);
+        const int jlo = fwd ? max(0, T - pn) : T + 2;
+        const int jhi = fwd ? T - 2 : min(a.S - 1, T + pn);
         VT acc[NRC];
 #pragma unroll
         for (int r = 0; r < NRC; ++r) acc[r] = VT(0);
@@ -306,7 +504,11 @@ __global__ void __launch_bounds__(kSThreads, 1) solve_kernel(SolveArgs a) {
         for (int idx = tid; idx < nr * kSB; idx += kSThreads) {
           const int r = idx / kSB, i = idx % kSB;
           VT s = tree_sum<kSWarps, VT>(&sm.red[0][r][i], NRC * kSB);
-          if (rank == 1) s -= (VT)sm.bpre[buf][r][i];
+          if (rank == 1) {
+            s -= (VT)sm.bpre[buf][r][i];
+            if (far_on && pos > a.dnear)
+              for (int f = 0; f < a.far; ++f) s += (VT)sm.fpre[buf][f][i];
+          }
           sm.vec[r][i] = s;
         }
         __syncthreads();
@@ -337,6 +539,13 @@ __global__ void __launch_bounds__(kSThreads, 1) solve_kernel(SolveArgs a) {
       cluster.sync();
       for (int pos = 0; pos < a.S; ++pos) {
         const int T = fwd ? pos : a.S - 1 - pos;
+        // the blocks of positions < pos are in the column (the leader stored them
+        // before the last cluster barrier): one worker thread publishes that count
+        // for the far clusters, up to the last position they read
+        if (far_on && rank == NW && tid == kSThreads - 32 && pos >= 1 && pos <= a.S - 1 - a.dnear) {
+          __threadfence();
+          st_relaxed(&a.fctl[0], (int)(base + pos));
+        }
         if (rank == 0) {
           // block T = -(M_T or N_T) * previous block - sum of the workers' shares
           const int buf = pos & 1;
@@ -398,6 +607,16 @@ static cudaError_t launch_columns(cudaLaunchConfig_t cfg, const SolveArgs& a) {
   if (e != cudaSuccess) return e;
   if (!ok) return cudaErrorInvalidConfiguration;
   cfg.dynamicSmemBytes = sizeof(SolveSmem<CL - 1, VT, NRC>);
+  if constexpr (CL == 16 && NRC == 1 && std::is_same<VT, double>::value) {
+    if (a.far > 0) {
+      e = cudaFuncSetAttribute(solve_kernel<CL, VT, NRC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)cfg.dynamicSmemBytes);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(solve_kernel<CL, VT, NRC, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+      return cudaLaunchKernelEx(&cfg, solve_kernel<CL, VT, NRC, true>, a);
+    }
+  }
   return cudaLaunchKernelEx(&cfg, solve_kernel<CL, VT, NRC>, a);
 }
 
@@ -440,6 +659,21 @@ static cudaError_t launch_cluster(const SolveArgs& a0, cudaStream_t stream, bool
   a.rhs_per = (a.nrhs + clusters - 1) / clusters;
   const int groups = (a.nrhs + a.rhs_per - 1) / a.rhs_per;
   cfg.gridDim = dim3(CL * groups);
+  // One column, 16-CTA clusters and block distances past 16: far clusters take
+  // the distances 17 .. P, one tile per CTA where the resident clusters allow
+  // (every cluster of the launch must be resident at once: the group's
+  // clusters wait on one another, with bounded waits).
+  if (CL == 16 && a.nrhs == 1 && a.fctl != nullptr && a.P > CL) {
+    const int nf = a.P - CL;   // distances CL + 1 .. P
+    int F = std::min((nf + CL - 1) / CL, std::min(kMaxF, clusters - 1));
+    if (F >= 1 && (nf + F * CL - 1) / (F * CL) <= kMaxT) {
+      e = cudaMemsetAsync(a.fctl, 0, kFarCtlBytes, stream);
+      if (e != cudaSuccess) return e;
+      a.far = F;
+      a.dnear = CL;
+      cfg.gridDim = dim3(CL * (1 + F));
+    }
+  }
   *fits = true;
   if (a.rhs_per == 1) return launch_columns<CL, VT, 1>(cfg, a);
   if (a.rhs_per == 2) return launch_columns<CL, VT, 2>(cfg, a);
@@ -447,9 +681,11 @@ static cudaError_t launch_cluster(const SolveArgs& a0, cudaStream_t stream, bool
   return launch_columns<CL, VT, NRC>(cfg, a);
 }
 
+// status / wait_ns: the status word and the wait limit of the far clusters'
+// bounded waits (status == nullptr: no far clusters).
 template <typename VT>
 static cudaError_t launch_solve_t(int n, int k, int nrhs, const double* ab, long long ldab, double* b, long long ldb,
-                                  void* ws, int* launches, cudaStream_t stream) {
+                                  void* ws, int* launches, cudaStream_t stream, int* status, uint64_t wait_ns) {
   *launches = 0;
   if (n <= 0 || nrhs <= 0) return cudaSuccess;
   if (k > n - 1) k = n - 1;
@@ -464,6 +700,13 @@ static cudaError_t launch_solve_t(int n, int k, int nrhs, const double* ab, long
   if (e != cudaSuccess) return e;
   *launches = 1;
   SolveArgs a{ab, ldab, n, k, S, P, b, ldb, nrhs, linv, mfw, nbw, 1, nrhs};
+  a.dnear = P;
+  if (status) {
+    a.fctl = reinterpret_cast<int*>(nbw + (size_t)S * kBlk);
+    a.fsum = reinterpret_cast<double*>(reinterpret_cast<char*>(a.fctl) + kFarCtlBytes);
+    a.status = status;
+    a.wait_ns = wait_ns;
+  }
   bool fits = false;
   // One column per cluster when 16-CTA clusters can cover all of them; else 8-CTA
   // clusters (more of them fit); else 16-CTA clusters with several columns each.
@@ -479,19 +722,20 @@ static cudaError_t launch_solve_t(int n, int k, int nrhs, const double* ab, long
 // Path of the FP64 solve: the partitioned chunk solve (psolve.cu) for
 // 1 <= k <= psolve_max_k() and at least eight chunks, where the cluster chain's
 // per-block latency dominates; the cluster solve otherwise.  path: 0 automatic,
-// 1 cluster, 2 partitioned (where it applies).
+// 1 cluster, 2 partitioned (where it applies), 3 cluster without far clusters.
 cudaError_t launch_solve(int n, int k, int nrhs, const double* ab, long long ldab, double* b, long long ldb, void* ws,
                          int* launches, cudaStream_t stream, int path, int* status, uint64_t wait_ns) {
   const int kk = (n > 0 && k > n - 1) ? n - 1 : k;
   const bool part_ok = kk >= 1 && kk <= psolve_max_k() && status != nullptr;
   const bool part = part_ok && (path == 2 || (path == 0 && n >= 8 * 256));
   if (part) return launch_psolve(n, kk, nrhs, ab, ldab, b, ldb, ws, status, wait_ns, launches, stream);
-  return launch_solve_t<double>(n, k, nrhs, ab, ldab, b, ldb, ws, launches, stream);
+  return launch_solve_t<double>(n, k, nrhs, ab, ldab, b, ldb, ws, launches, stream, path == 3 ? nullptr : status,
+                                wait_ns);
 }
 
 cudaError_t launch_solve_f32(int n, int k, int nrhs, const double* ab, long long ldab, double* b, long long ldb,
                              void* ws, int* launches, cudaStream_t stream) {
-  return launch_solve_t<float>(n, k, nrhs, ab, ldab, b, ldb, ws, launches, stream);
+  return launch_solve_t<float>(n, k, nrhs, ab, ldab, b, ldb, ws, launches, stream, nullptr, 0);
 }
 
 }  // namespace bchol

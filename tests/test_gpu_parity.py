@@ -292,3 +292,34 @@ def test_tile_staging_arguments():
     with pytest.raises(bchol.BcholError):
         h.set_tile_staging(2)
     assert h.last_tile_staging() == 0   # nothing factored yet
+
+
+@pytest.mark.parametrize("n,k", [(9000, 530), (12001, 1000), (6000, 2000), (3000, 2999), (8000, 3100)])
+def test_far_cluster_solve_matches_oracle(n, k):
+    """One-column solves with more than 16 blocks of band below the diagonal run
+    the far block distances on extra clusters (solve path 1, the default there).
+    x against the oracle's substitution on the exact factor, and against the
+    same solve on one cluster (path 3), over two calls in a row (the far
+    clusters' control words are cleared before every launch)."""
+    L0, A, B = g.problem(n, k, seed=n + k, diag="log1e3", exact=True)
+    xref = oracle.pbtrs(L0, k, B[:, 0])
+    h = bchol.Handle()
+    ab = bchol.band_from_numpy(A)
+    bchol.factor(ab, k, handle=h)
+    out = {}
+    for path in (1, 3):
+        h.set_solve_path(path)
+        for call in range(2):
+            b = torch.from_numpy(B[:, 0].copy()).cuda()
+            bchol.solve(ab, k, b, handle=h)
+            rc, _ = bchol.get_info(torch.zeros(1, dtype=torch.int32, device="cuda"), handle=h)
+            assert rc == 0
+            x = b.cpu().numpy()
+            ex = float(np.linalg.norm(x - xref) / np.linalg.norm(xref))
+            print(f"n={n} k={k} path {path} call {call}: rel err x {ex:.2e}")
+            assert ex <= TOL_X
+            out[(path, call)] = x
+    d = float(np.linalg.norm(out[(1, 1)] - out[(3, 1)]) / np.linalg.norm(out[(3, 1)]))
+    print(f"far clusters against one cluster: rel diff {d:.2e}")
+    assert d <= 1e-12
+    assert np.array_equal(out[(1, 0)], out[(1, 1)])
